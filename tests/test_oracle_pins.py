@@ -1,0 +1,374 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests re-types an oracle formula: each checks the oracle
+against a printed example (tests/golden), a library routine run on a
+different route, a closed form, an invariant proved in the paper, or brute
+force on tiny inputs.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize
+
+import workloads as wl
+from oracle import method as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2 / 3.2 printed matrices
+# --------------------------------------------------------------------------
+
+def test_toeplitz_matches_printed_H():
+    # Eq. (Toeplitz)
+    np.testing.assert_array_equal(O.toeplitz_D(5), _load("toeplitz_H_m5.txt"))
+
+
+def test_dtd_matches_printed_matrix_and_spectrum_bounds():
+    # Proposition "KKProp": printed D^T D, lambda_min = 0, lambda_max <= 4
+    D = O.toeplitz_D(6)
+    np.testing.assert_array_equal(D.T @ D, _load("dtd_m6.txt"))
+    for m in (2, 3, 7, 48, 144):
+        D = O.toeplitz_D(m)
+        lam = np.linalg.eigvalsh(D.T @ D)
+        # closed form of the path-graph Laplacian: 2 - 2 cos(pi j / m)
+        closed = np.sort(2.0 - 2.0 * np.cos(math.pi * np.arange(m) / m))
+        np.testing.assert_allclose(np.sort(lam), closed, atol=1e-12)
+        assert abs(lam.min()) < 1e-12 and lam.max() <= 4.0
+
+
+def test_bcirc_block_pattern_matches_printed_layout():
+    m1, m2, m3 = 2, 3, 5
+    A = np.zeros((m1, m2, m3))
+    for j in range(m3):
+        A[:, :, j] = j + 1  # slice j (0-based) filled with its 1-based number
+    B = O.bcirc(A)
+    blocks = np.array([[B[k * m1, l * m2] for l in range(m3)] for k in range(m3)])
+    np.testing.assert_array_equal(blocks, _load("bcirc_blocks_m3_5.txt"))
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2: DFT, t-product, conjugate symmetry
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m3", [1, 2, 5, 7, 8])
+def test_dft3_against_numpy_fft(m3):
+    A = _rng(m3).standard_normal((3, 4, m3))
+    # omega = exp(+2 pi i / m3): sum_l omega^(kl) A_l = m3 * ifft(A)_k
+    np.testing.assert_allclose(O.dft3(A), m3 * np.fft.ifft(A, axis=2), atol=1e-12)
+    np.testing.assert_allclose(O.dft3(A, sign=-1), np.fft.fft(A, axis=2), atol=1e-12)
+    np.testing.assert_allclose(O.idft3(O.dft3(A)).real, A, atol=1e-12)
+
+
+def test_orthogonality_sum_lsm3():
+    # Eq. (lsm3): sum_k omega^{(k)(l)} conj(omega)^{(k)(s)} = m3 delta_ls
+    for m3 in (3, 6, 7):
+        F = O.dft_matrix(m3)
+        np.testing.assert_allclose(F.T @ np.conj(F), m3 * np.eye(m3), atol=1e-12)
+
+
+@pytest.mark.parametrize("m3", [1, 4, 5, 7])
+def test_tproduct_slices_equal_bcirc_definition(m3):
+    rng = _rng(10 + m3)
+    A = rng.standard_normal((4, 3, m3))
+    B = rng.standard_normal((3, 5, m3))
+    np.testing.assert_allclose(O.tprod(A, B), O.tprod_definition(A, B), rtol=1e-13, atol=1e-13)
+    # Eq. (BDFT): (F (x) I) bcirc(A) (F^* (x) I) is block diagonal with A~_k
+    F = O.dft_matrix(m3) / math.sqrt(m3)
+    L = np.kron(F, np.eye(4)) @ O.bcirc(A) @ np.kron(np.conj(F).T, np.eye(3))
+    At = O.dft3(A)
+    for k in range(m3):
+        np.testing.assert_allclose(L[4 * k:4 * k + 4, 3 * k:3 * k + 3], At[:, :, k], atol=1e-12)
+
+
+@pytest.mark.parametrize("m3", [6, 7])
+def test_conjugate_symmetry_of_real_spectrum(m3):
+    # Eq. (rcm_3-k+2): A~_1 real, A~_k = conj(A~_{m3-k+2})
+    A = _rng(3).standard_normal((3, 4, m3))
+    At = O.dft3(A)
+    assert np.max(np.abs(At[:, :, 0].imag)) < 1e-12
+    for k in range(1, m3):
+        np.testing.assert_allclose(At[:, :, k], np.conj(At[:, :, m3 - k]), atol=1e-12)
+    np.testing.assert_allclose(O.mirror_half(At[:, :, : m3 // 2 + 1], m3), At, atol=1e-12)
+
+
+def test_tubal_rank_of_generated_truth():
+    # Proposition "tubrank": rank_t(A*B) <= r; every DFT slice of the generated
+    # truth has rank <= r
+    w = wl.custom(12, 20, 6, 3, 0.5, 99)
+    inst = wl.generate(w)
+    Tt = O.dft3(inst["T"])
+    for k in range(w.n3):
+        sv = np.linalg.svd(Tt[:, :, k], compute_uv=False)
+        assert sv[w.r] < 1e-10 * sv[0]
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.3: Parseval form of f0
+# --------------------------------------------------------------------------
+
+def test_objective_spatial_equals_frequency_form():
+    rng = _rng(5)
+    m1, m2, m3, r = 6, 7, 5, 2
+    X = rng.standard_normal((m1, r, m3))
+    Y = rng.standard_normal((r, m2, m3))
+    W = rng.standard_normal((m1, m2, m3))
+    mu, rho1, rho2 = 0.3, 0.7, 1.1
+    f_sp = O.objective(X, Y, W, mu, rho1, rho2)
+    f_fr = O.objective_freq(O.dft3(X), O.dft3(Y), O.dft3(W), mu, rho1, rho2)
+    assert abs(f_sp - f_fr) < 1e-11 * abs(f_sp)
+    # brute-force spatial form: explicit sums of squared neighbour differences
+    Z = O.tprod_definition(X, Y)
+    brute = 0.5 * np.sum((Z - W) ** 2) + 0.5 * mu * np.sum(W ** 2)
+    brute += 0.5 * rho1 * np.sum((Z[:-1, :, :] - Z[1:, :, :]) ** 2)
+    brute += 0.5 * rho2 * np.sum((W[:, :-1, :] - W[:, 1:, :]) ** 2)
+    assert abs(f_sp - brute) < 1e-11 * abs(brute)
+
+
+# --------------------------------------------------------------------------
+# Lemma "SVPMPI": pseudo-inverse
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rank", [1, 3, 5])
+def test_pinv_penrose_conditions(rank):
+    rng = _rng(rank)
+    r = 5
+    F = rng.standard_normal((r, rank)) + 1j * rng.standard_normal((r, rank))
+    A = F @ F.conj().T
+    P = O.pinv_herm(A)
+    scale = np.linalg.norm(A) * np.linalg.norm(P)
+    assert np.linalg.norm(A @ P @ A - A) < 1e-12 * scale * np.linalg.norm(A)
+    assert np.linalg.norm(P @ A @ P - P) < 1e-12 * scale * np.linalg.norm(P)
+    assert np.linalg.norm((A @ P).conj().T - A @ P) < 1e-12 * scale
+    assert np.linalg.norm((P @ A).conj().T - P @ A) < 1e-12 * scale
+    np.testing.assert_allclose(P, np.linalg.pinv(A, rcond=1e-10, hermitian=True), atol=1e-10 * np.abs(P).max())
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.3: the W sub-problem
+# --------------------------------------------------------------------------
+
+def _wcase(seed=7, m1=4, m2=9, m3=3, p=0.4):
+    rng = _rng(seed)
+    Z = rng.standard_normal((m1, m2, m3))
+    G = rng.standard_normal((m1, m2, m3))
+    mask = rng.random((m1, m2, m3)) < p
+    mask[0, :, 0] = True  # a fully observed row
+    mask[1, :, 0] = False  # a fully missing row
+    return Z, G, mask
+
+
+@pytest.mark.parametrize("mu,rho2", [(0.0, 0.0), (1e-3, 0.1), (0.5, 3.0)])
+def test_wstep_minimises_g_k_bruteforce(mu, rho2):
+    # Eq. (WETP-optim20): W_k minimises g_k over the missing entries; compare
+    # with a generic numerical minimiser of g_k written from its definition.
+    Z, G, mask = _wcase()
+    m1, m2, m3 = Z.shape
+    K = O.toeplitz_D(m2)
+    W = O.w_step_dense(Z, G, mask, mu, rho2)
+    for k in range(m3):
+        for i in range(m1):
+            C = np.flatnonzero(~mask[i, :, k])
+            if C.size == 0:
+                np.testing.assert_array_equal(W[i, :, k], G[i, :, k])
+                continue
+
+            def g(v):
+                w = np.where(mask[i, :, k], G[i, :, k], 0.0)
+                w[C] = v
+                return 0.5 * (np.sum((Z[i, :, k] - w) ** 2) + rho2 * np.sum((K @ w) ** 2) + mu * np.sum(w ** 2))
+
+            res = scipy.optimize.minimize(g, np.zeros(C.size), method="BFGS", options={"gtol": 1e-12})
+            np.testing.assert_allclose(W[i, C, k], res.x, atol=1e-6)
+            np.testing.assert_array_equal(W[i, mask[i, :, k], k], G[i, mask[i, :, k], k])
+
+
+@pytest.mark.parametrize("mu,rho2", [(0.0, 0.0), (1e-3, 0.1), (0.5, 3.0)])
+def test_wstep_kkt_banded_equals_dense_and_kkt_residual(mu, rho2):
+    Z, G, mask = _wcase(11, 5, 13, 4)
+    Wd = O.w_step_dense(Z, G, mask, mu, rho2)
+    Wb = O.w_step_kkt(Z, G, mask, mu, rho2)
+    np.testing.assert_allclose(Wb, Wd, rtol=1e-12, atol=1e-12)
+    # Eq. (subquKKT): (W_k K_{mu rho2})_ij = (Z_k)_ij off the mask
+    Kmr = O.K_murho(Z.shape[1], mu, rho2)
+    for k in range(Z.shape[2]):
+        lhs = Wd[:, :, k] @ Kmr
+        miss = ~mask[:, :, k]
+        np.testing.assert_allclose(lhs[miss], Z[:, :, k][miss], atol=1e-12)
+
+
+def test_wstep_closed_form_without_periodicity_term():
+    # rho2 = 0: g_k separates per entry, W = Z / (1 + mu) off the mask
+    Z, G, mask = _wcase(2)
+    W = O.w_step_kkt(Z, G, mask, 0.25, 0.0)
+    np.testing.assert_allclose(W[~mask], Z[~mask] / 1.25, atol=1e-14)
+    np.testing.assert_array_equal(W[mask], G[mask])
+
+
+def test_wz_gap_bound():
+    # bound after Proposition "KKProp": sum ||(W-Z)_{Omega^c}|| <= (mu+4 rho2) sum ||W_k||
+    Z, G, mask = _wcase(3, 6, 20, 5, 0.3)
+    for mu, rho2 in ((1e-3, 0.1), (0.2, 1.0)):
+        W = O.w_step_kkt(Z, G, mask, mu, rho2)
+        lhs = sum(np.linalg.norm((W[:, :, k] - Z[:, :, k]) * ~mask[:, :, k]) for k in range(Z.shape[2]))
+        rhs = (mu + 4 * rho2) * sum(np.linalg.norm(W[:, :, k]) for k in range(Z.shape[2]))
+        assert lhs <= rhs
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.1: gradients, exact steps and the KKT system
+# --------------------------------------------------------------------------
+
+def _slice_case(seed=4, m1=6, m2=8, r=3):
+    rng = _rng(seed)
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)  # noqa: E731
+    return c(m1, r), c(r, m2), c(m1, m2)
+
+
+def test_slice_gradients_against_finite_differences():
+    # Eq. (hkXYDer) under Theorem "PDconj": the stated gradient equals
+    # d h/d Re + i d h/d Im of the real function h_k (central differences).
+    X, Y, W = _slice_case()
+    rho1 = 0.7
+    m1 = X.shape[0]
+    H = O.toeplitz_D(m1)
+
+    def h(Xv, Yv):
+        Z = Xv @ Yv
+        return 0.5 * (np.sum(np.abs(Z - W) ** 2) + rho1 * np.sum(np.abs(H @ Z) ** 2))
+
+    eps = 1e-6
+    for name, grad, arr in (("X", O.grad_X(X, Y, W, rho1), X), ("Y", O.grad_Y(X, Y, W, rho1), Y)):
+        fd = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            for part, unit in ((1.0, 1.0), (1j, 1j)):
+                P = arr.copy()
+                P[idx] += eps * unit
+                M = arr.copy()
+                M[idx] -= eps * unit
+                args_p = (P, Y) if name == "X" else (X, P)
+                args_m = (M, Y) if name == "X" else (X, M)
+                fd[idx] += part * (h(*args_p) - h(*args_m)) / (2 * eps)
+        np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-6)
+
+
+def test_exact_steps_solve_kkt_system():
+    # Eq. (KKTcondition): with full-rank Y and X the exact X-step satisfies
+    # H_rho1 X (Y Y^*) = W Y^*, and the exact Y-step (X^* H_rho1 X) Y = X^* W.
+    X, Y, W = _slice_case(8)
+    rho1 = 0.4
+    Hr = O.H_rho(X.shape[0], rho1)
+    Xn = O.x_update(X, Y, W, rho1)
+    lhs, rhs = Hr @ Xn @ (Y @ Y.conj().T), W @ Y.conj().T
+    assert np.linalg.norm(lhs - rhs) < 1e-10 * np.linalg.norm(rhs)
+    Yn = O.y_update(Xn, Y, W, rho1)
+    lhs, rhs = (Xn.conj().T @ Hr @ Xn) @ Yn, Xn.conj().T @ W
+    assert np.linalg.norm(lhs - rhs) < 1e-10 * np.linalg.norm(rhs)
+
+
+def test_scaled_steps_are_descent_directions():
+    # Propositions "DirecX" / "DirecY": d_X, d_Y are descent directions; a
+    # small scaled step decreases h_k
+    X, Y, W = _slice_case(9)
+    rho1 = 0.3
+    H = O.toeplitz_D(X.shape[0])
+
+    def h(Xv, Yv):
+        Z = Xv @ Yv
+        return 0.5 * (np.sum(np.abs(Z - W) ** 2) + rho1 * np.sum(np.abs(H @ Z) ** 2))
+
+    Xn = O.x_update(X, Y, W, rho1, step="scaled", alpha=0.5)
+    assert h(Xn, Y) < h(X, Y)
+    Yn = O.y_update(Xn, Y, W, rho1, step="scaled", beta=0.5)
+    assert h(Xn, Yn) < h(Xn, Y)
+
+
+# --------------------------------------------------------------------------
+# The TCTF2R Algorithm: invariants and special cases
+# --------------------------------------------------------------------------
+
+def test_objective_monotone_at_every_half_step():
+    # Theorem "GlobConvergM" and Proposition "inWWk"
+    w = wl.custom(10, 16, 7, 2, 0.4, 321, iters=15)
+    inst = wl.generate(w)
+    out = O.tctf2r(inst["G"], inst["mask"], w.r, 1e-3, 0.05, 0.2, inst["Y0"], iters=15, record=True)
+    h = out["hist"]
+    seq = []
+    for a, b, c in zip(h["f0_after_x"], h["f0_after_y"], h["f0"]):
+        seq += [a, b, c]
+    d = np.diff(seq)
+    assert np.all(d <= 1e-10 * np.abs(np.array(seq[:-1])))
+
+
+def test_exact_recovery_fully_observed_rank_r():
+    # Proposition "tubrank": a noise-free tensor of tubal rank r, fully
+    # observed, mu = rho = 0, is recovered to machine precision
+    rng = _rng(12)
+    A = rng.standard_normal((9, 2, 5))
+    B = rng.standard_normal((2, 11, 5))
+    T = O.tprod_definition(A, B)
+    mask = np.ones(T.shape, bool)
+    out = O.tctf2r(T, mask, 2, 0.0, 0.0, 0.0, rng.standard_normal((2, 11, 5)), iters=30)
+    assert np.linalg.norm(out["Z"] - T) <= 1e-10 * np.linalg.norm(T)
+
+
+def test_converged_objective_equals_eckart_young():
+    # fully observed, mu = rho = 0: the optimum of Eq. (fun-XYW) is the best
+    # rank-r approximation of every slice, f0 = (1/2m3) sum_k sum_{i>r} sigma_i^2
+    rng = _rng(13)
+    M = rng.standard_normal((8, 10, 5))
+    mask = np.ones(M.shape, bool)
+    r = 2
+    out = O.tctf2r(M, mask, r, 0.0, 0.0, 0.0, rng.standard_normal((r, 10, 5)), iters=400)
+    Mt = O.dft3(M)
+    ey = sum(np.sum(np.linalg.svd(Mt[:, :, k], compute_uv=False)[r:] ** 2) for k in range(5)) / 10.0
+    assert abs(out["f0"] - ey) <= 1e-8 * ey
+
+
+def test_half_spectrum_equals_full_spectrum():
+    # remark after the TCTF2R Algorithm: floor(m3/2)+1 slices suffice
+    for n3 in (6, 7):
+        w = wl.custom(7, 9, n3, 2, 0.5, 50 + n3, iters=6)
+        inst = wl.generate(w)
+        a = O.tctf2r(inst["G"], inst["mask"], 2, 1e-2, 0.1, 0.3, inst["Y0"], iters=6, half=True)
+        b = O.tctf2r(inst["G"], inst["mask"], 2, 1e-2, 0.1, 0.3, inst["Y0"], iters=6, half=False)
+        np.testing.assert_allclose(a["W"], b["W"], rtol=1e-10, atol=1e-10)
+
+
+def test_dft_sign_convention_does_not_change_real_outputs():
+    w = wl.custom(6, 10, 5, 2, 0.5, 77, iters=5)
+    inst = wl.generate(w)
+    a = O.tctf2r(inst["G"], inst["mask"], 2, 1e-2, 0.1, 0.3, inst["Y0"], iters=5, sign=+1)
+    b = O.tctf2r(inst["G"], inst["mask"], 2, 1e-2, 0.1, 0.3, inst["Y0"], iters=5, sign=-1)
+    np.testing.assert_allclose(a["W"], b["W"], rtol=1e-10, atol=1e-10)
+    assert abs(a["f0"] - b["f0"]) < 1e-10 * a["f0"]
+
+
+def test_matrix_case_m3_1_is_rank_r_fit():
+    # m3 = 1: the model is plain matrix factorisation; fully observed and
+    # mu = rho = 0 it converges to the truncated SVD (numpy)
+    rng = _rng(21)
+    M = rng.standard_normal((7, 9, 1))
+    out = O.tctf2r(M, np.ones(M.shape, bool), 2, 0.0, 0.0, 0.0, rng.standard_normal((2, 9, 1)), iters=500)
+    U, s, Vh = np.linalg.svd(M[:, :, 0])
+    best = (U[:, :2] * s[:2]) @ Vh[:2]
+    np.testing.assert_allclose(out["Z"][:, :, 0], best, atol=1e-7)
+
+
+def test_dense_and_banded_wstep_agree_in_the_loop():
+    w = wl.custom(5, 12, 4, 2, 0.4, 31, iters=4)
+    inst = wl.generate(w)
+    a = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 0.1, 0.5, inst["Y0"], iters=4, wstep="dense")
+    b = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 0.1, 0.5, inst["Y0"], iters=4, wstep="kkt")
+    np.testing.assert_allclose(a["W"], b["W"], rtol=1e-11, atol=1e-11)
