@@ -1,0 +1,141 @@
+/*
+ * tctf2r.h -- C ABI of the GB300 TCTF2R traffic-tensor completion library.
+ *
+ * The library runs the per-iteration hot path of the TCTF2R Algorithm
+ * (arXiv 2005.09838, Sec. 4.1) on one CUDA device: the generalized-inverse
+ * X/Y updates of every frequency slice (Eq. (updataXYW1)), the product
+ * Z~_k = X~_k Y~_k and its inverse mode-3 DFT (Eq. (barAAk)), the W-update
+ * (Eq. (subquKKT) / Eq. (Wkiom)) and the forward mode-3 DFT of the new W
+ * (Eq. (bar BA-k)).  Only floor(n3/2)+1 slices are solved; the others are
+ * their complex conjugates (remark after the TCTF2R Algorithm).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a tc_status; none aborts or exits.  On failure
+ *    tc_last_error() returns a message (thread-local, valid until the next
+ *    call from the same thread).
+ *  - Tensors are dense, column-major with the first index fastest: element
+ *    (i1, i2, i3) of an n1 x n2 x n3 tensor is at i1 + n1*(i2 + n2*i3).  This
+ *    is the element order of the paper's unfold (Sec. 2.1).
+ *  - Real element type follows tc_params.precision: double for TC_FP64,
+ *    float for TC_FP32.
+ *  - The caller owns every pointer it passes; the library copies what it
+ *    needs and never keeps a caller pointer past the call.
+ *  - A context is bound to the CUDA device that was current at tc_init and to
+ *    the stream given there; all work is stream-ordered on that stream.  A
+ *    context must not be used from two host threads at once.
+ *  - After TC_ERR_CUDA or TC_ERR_TIMEOUT a context is poisoned: every later
+ *    call on it returns TC_ERR_STATE except tc_free.
+ */
+#ifndef TCTF2R_H
+#define TCTF2R_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_ARG = 1,         /* invalid argument (sizes, NULL pointers, ranges) */
+  TC_ERR_NOMEM = 2,       /* device or host allocation failed */
+  TC_ERR_CUDA = 3,        /* a CUDA runtime call or kernel failed */
+  TC_ERR_NUMERIC = 4,     /* non-finite objective or state */
+  TC_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  TC_ERR_STATE = 6,       /* context poisoned by an earlier error */
+  TC_ERR_UNSUPPORTED = 7  /* option not implemented by this build */
+} tc_status;
+
+typedef enum { TC_FP64 = 0, TC_FP32 = 1, TC_TF32 = 2, TC_BF16 = 3 } tc_precision;
+
+/* Step rule of Eq. (updataXYW1).  TC_STEP_EXACT takes alpha_kl = L_k1 and
+ * beta_kl = L_k2 (unit steps along d_X, d_Y: exact minimisation of the
+ * quadratic h_k in each block).  TC_STEP_SCALED uses the fixed alpha, beta
+ * below divided by L_k1 = ||H_rho1||_2 ||Y~Y~^*||_2 and L_k2 = ||X~^* H_rho1 X~||_2. */
+typedef enum { TC_STEP_EXACT = 0, TC_STEP_SCALED = 1 } tc_step;
+
+/* Problem statement of the TCTF2R Algorithm (Sec. 4.1, "Input").  H and K are
+ * the fixed first-difference matrices of Eq. (Toeplitz) acting on modes 1 and
+ * 2, so they are implied by n1 and n2.  Layout: 96 bytes, no implicit padding. */
+typedef struct {
+  int64_t n1, n2, n3;  /* tensor sizes (paper m1, m2, m3), each >= 1 */
+  int32_t r;           /* tubal rank, 1 <= r <= min(n1, n2, 32) */
+  int32_t precision;   /* tc_precision: TC_FP64 or TC_FP32 in this build */
+  double mu;           /* weight of ||W||^2, >= 0 (Eq. (TETP-optim)) */
+  double rho1;         /* weight of the temporal-stability term on mode 1, >= 0 */
+  double rho2;         /* weight of the periodicity term on mode 2, >= 0 */
+  int32_t step;        /* tc_step */
+  int32_t flags;       /* reserved, must be 0 */
+  double alpha, beta;  /* step sizes, used only with TC_STEP_SCALED, > 0 */
+  double eps;          /* stopping tolerance of step 6; 0 = run exactly n iterations */
+  double pinv_rtol;    /* Gram eigenvalues <= pinv_rtol * lambda_max are cut by the
+                          pseudo-inverse; <= 0 selects r * 2^-52 */
+} tc_params;
+
+typedef struct tc_ctx tc_ctx;
+
+/* Create a context and set the initial point of the TCTF2R Algorithm
+ * ("Initialize"): W0 = P_Omega(G) (Sec. 3.1, missing entries filled with 0),
+ * Y~0 and X~0 the mode-3 DFTs (Eq. (bar BA-k)) of Y0 and X0.
+ *   out    : receives the new context (set to NULL on failure)
+ *   p      : parameters, copied
+ *   G      : n1*n2*n3 reals, observed tensor; entries off the mask are ignored
+ *   mask   : n1*n2*n3 bytes, nonzero = observed (the set Omega)
+ *   Y0     : r*n2*n3 reals, initial factor Y in the spatial domain (required)
+ *   X0     : n1*r*n3 reals, initial factor X, or NULL for zero
+ *   inputs_on_device : 1 if G, mask, Y0, X0 are device pointers on the current
+ *            device, 0 if they are host pointers
+ *   cuda_stream : cudaStream_t to order all work on (NULL = legacy default)
+ * Device memory of the context is allocated here (cudaMalloc) and released by
+ * tc_free.  Synchronises the stream before returning.
+ * Errors: TC_ERR_ARG for invalid sizes/parameters/NULL inputs, TC_ERR_NOMEM,
+ * TC_ERR_CUDA, TC_ERR_UNSUPPORTED for precisions or options not built. */
+tc_status tc_init(tc_ctx** out, const tc_params* p, const void* G, const uint8_t* mask,
+                  const void* Y0, const void* X0, int32_t inputs_on_device, void* cuda_stream);
+
+/* Run n_iters iterations of the TCTF2R Algorithm (steps 1-4 and 7 of Sec. 4.1;
+ * step 5 keeps r fixed).  Asynchronous: work is enqueued on the context's
+ * stream and the call returns without waiting, unless p->eps > 0, in which case
+ * the stopping test of step 6 is evaluated after every iteration (with a device
+ * synchronisation) and the loop ends early when it holds.
+ *   done : receives the number of iterations run (may be NULL)
+ * Errors: TC_ERR_ARG (n_iters < 0), TC_ERR_CUDA, TC_ERR_STATE. */
+tc_status tc_iterate(tc_ctx* c, int32_t n_iters, int32_t* done);
+
+/* Objective f0 of Eq. (TETP-optim) at the current iterate (X, Y, W), reduced in
+ * FP64, and optionally ||P_Omega(X*Y - G)||_F.  Synchronises the stream.
+ *   f0        : receives f0 (required)
+ *   resid_obs : receives the observed-entry residual norm (may be NULL)
+ * Errors: TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_NUMERIC (non-finite f0), TC_ERR_STATE. */
+tc_status tc_objective(tc_ctx* c, double* f0, double* resid_obs);
+
+/* Copy the current iterate out (TCTF2R Algorithm, "Output"): W (n1*n2*n3 reals),
+ * and optionally the spatial factors X (n1*r*n3) and Y (r*n2*n3), in the
+ * column-major layout above.  dst_on_device selects device or host buffers.
+ * Synchronises the stream.  Errors: TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_STATE. */
+tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device);
+
+/* Profiling aid: run n_iters real iterations (they advance the state exactly
+ * like tc_iterate) but launch the three per-iteration kernels one by one, with
+ * CUDA events recorded around each on the context's stream, then synchronise.
+ *   ms : receives 3 values, the mean device time per launch in milliseconds of
+ *        the X-step kernel, the Y-step kernel and the slab kernel (fused
+ *        synthesis / inverse DFT / W-step / forward DFT / X-contraction).
+ * Errors: TC_ERR_ARG (n_iters < 1 or ms NULL), TC_ERR_CUDA, TC_ERR_STATE. */
+tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
+
+/* Release a context and its device memory.  NULL-safe.  Synchronises the
+ * context's stream first. */
+tc_status tc_free(tc_ctx* c);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* tc_last_error(void);
+
+/* Library version string. */
+const char* tc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCTF2R_H */

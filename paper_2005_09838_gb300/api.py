@@ -1,0 +1,44 @@
+"""Convenience wrapper: numpy tensors indexed [i1, i2, i3] in, numpy out.
+
+Marshalling only (layout conversion to the C ABI's column-major order and
+back); the completion itself runs in libtctf2r.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import tc
+
+
+def _colmajor(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a).transpose(2, 1, 0)).astype(dtype, copy=False).reshape(-1)
+
+
+def _from_colmajor(flat: np.ndarray, shape) -> np.ndarray:
+    a, b, c = shape
+    return flat.reshape(c, b, a).transpose(2, 1, 0)
+
+
+def complete(G, mask, Y0, r, iters, mu=0.0, rho1=0.0, rho2=0.0, precision="fp32", X0=None,
+             want_factors=False, objective=True):
+    """Run ``iters`` TCTF2R iterations on the GPU.  Returns a dict with W (and
+    X, Y spatial with ``want_factors``), f0 and resid_obs."""
+    prec = {"fp32": tc.TC_FP32, "fp64": tc.TC_FP64}[precision]
+    dt = np.float64 if prec == tc.TC_FP64 else np.float32
+    n1, n2, n3 = G.shape
+    p = tc.make_params(n1, n2, n3, r, mu=mu, rho1=rho1, rho2=rho2, precision=prec)
+    g = _colmajor(G, dt)
+    m = _colmajor(np.asarray(mask, dtype=bool), np.uint8)
+    y = _colmajor(Y0, dt)
+    x = None if X0 is None else _colmajor(X0, dt)
+    with tc.Completion(p, g, m, y, x) as c:
+        c.iterate(iters)
+        out = {}
+        if objective:
+            out["f0"], out["resid_obs"] = c.objective()
+        W, X, Y = c.result_numpy(want_factors)
+        out["W"] = _from_colmajor(W, (n1, n2, n3)).astype(np.float64)
+        if want_factors:
+            out["X"] = _from_colmajor(X, (n1, r, n3)).astype(np.float64)
+            out["Y"] = _from_colmajor(Y, (r, n2, n3)).astype(np.float64)
+    return out

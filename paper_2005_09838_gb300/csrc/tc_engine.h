@@ -1,0 +1,28 @@
+// Host-side engine interface shared by the C ABI layer and the per-precision
+// translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tctf2r.h"
+
+namespace tc {
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+  virtual tc_status init(const tc_params& p, const void* G, const uint8_t* mask, const void* Y0, const void* X0,
+                         bool on_device, cudaStream_t stream, std::string& err) = 0;
+  virtual tc_status iterate(int n, int* done, std::string& err) = 0;
+  virtual tc_status objective(double* f0, double* resid_obs, std::string& err) = 0;
+  virtual tc_status result(void* W, void* X, void* Y, bool on_device, std::string& err) = 0;
+  virtual tc_status profile(int n, double* ms, std::string& err) = 0;
+  virtual void release() = 0;
+};
+
+EngineBase* make_engine_f32();
+EngineBase* make_engine_f64();
+
+}  // namespace tc

@@ -1,0 +1,174 @@
+"""Thin ctypes binding of the C ABI in include/tctf2r.h.
+
+Argument marshalling only: every step of the method runs in libtctf2r.so.
+The library is loaded on first use; if it is missing the call raises
+(there is no CPU fallback).  Arrays are passed as raw pointers: numpy arrays
+(host) or torch tensors (host or device) in the C ABI's column-major element
+order (first index fastest).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtctf2r.so")
+
+TC_OK, TC_ERR_ARG, TC_ERR_NOMEM, TC_ERR_CUDA, TC_ERR_NUMERIC, TC_ERR_TIMEOUT, TC_ERR_STATE, TC_ERR_UNSUPPORTED = range(8)
+TC_FP64, TC_FP32, TC_TF32, TC_BF16 = range(4)
+TC_STEP_EXACT, TC_STEP_SCALED = range(2)
+
+STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_ARG", 2: "TC_ERR_NOMEM", 3: "TC_ERR_CUDA", 4: "TC_ERR_NUMERIC",
+                5: "TC_ERR_TIMEOUT", 6: "TC_ERR_STATE", 7: "TC_ERR_UNSUPPORTED"}
+
+# Entry points declared in include/tctf2r.h (checked by the tests).
+EXPORTS = ("tc_init", "tc_iterate", "tc_objective", "tc_result", "tc_profile", "tc_free", "tc_last_error",
+           "tc_version")
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [
+        ("n1", ctypes.c_int64), ("n2", ctypes.c_int64), ("n3", ctypes.c_int64),
+        ("r", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("mu", ctypes.c_double), ("rho1", ctypes.c_double), ("rho2", ctypes.c_double),
+        ("step", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+        ("eps", ctypes.c_double), ("pinv_rtol", ctypes.c_double),
+    ]
+
+
+assert ctypes.sizeof(tc_params) == 96
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtctf2r.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2005_09838_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.tc_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(tc_params), P, P, P, P, ctypes.c_int32, P]
+    lib.tc_init.restype = ctypes.c_int
+    lib.tc_iterate.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.tc_iterate.restype = ctypes.c_int
+    lib.tc_objective.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.tc_objective.restype = ctypes.c_int
+    lib.tc_result.argtypes = [P, P, P, P, ctypes.c_int32]
+    lib.tc_result.restype = ctypes.c_int
+    lib.tc_profile.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    lib.tc_profile.restype = ctypes.c_int
+    lib.tc_free.argtypes = [P]
+    lib.tc_free.restype = ctypes.c_int
+    lib.tc_last_error.argtypes = []
+    lib.tc_last_error.restype = ctypes.c_char_p
+    lib.tc_version.argtypes = []
+    lib.tc_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TC_OK:
+        msg = load().tc_last_error().decode(errors="replace")
+        raise TCError(status, msg)
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be contiguous flat arrays in column-major element order")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous flat buffers in column-major element order")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def make_params(n1, n2, n3, r, mu=0.0, rho1=0.0, rho2=0.0, precision=TC_FP32, step=TC_STEP_EXACT,
+                alpha=1.0, beta=1.0, eps=0.0, pinv_rtol=0.0) -> tc_params:
+    return tc_params(n1, n2, n3, r, precision, mu, rho1, rho2, step, 0, alpha, beta, eps, pinv_rtol)
+
+
+class Completion:
+    """One TCTF2R context (tc_init ... tc_free)."""
+
+    def __init__(self, params: tc_params, G, mask, Y0, X0=None, on_device: bool = False, stream: int | None = None):
+        lib = load()
+        self._lib = lib
+        self.params = params
+        self._ctx = ctypes.c_void_p()
+        st = lib.tc_init(ctypes.byref(self._ctx), ctypes.byref(params), _ptr(G), _ptr(mask), _ptr(Y0), _ptr(X0),
+                         1 if on_device else 0, stream)
+        _check(st)
+
+    @property
+    def dtype(self):
+        return np.float64 if self.params.precision == TC_FP64 else np.float32
+
+    def iterate(self, n: int) -> int:
+        done = ctypes.c_int32(0)
+        _check(self._lib.tc_iterate(self._ctx, int(n), ctypes.byref(done)))
+        return done.value
+
+    def objective(self):
+        f0 = ctypes.c_double()
+        res = ctypes.c_double()
+        _check(self._lib.tc_objective(self._ctx, ctypes.byref(f0), ctypes.byref(res)))
+        return f0.value, res.value
+
+    def result(self, W=None, X=None, Y=None, on_device: bool = False):
+        _check(self._lib.tc_result(self._ctx, _ptr(W), _ptr(X), _ptr(Y), 1 if on_device else 0))
+
+    def result_numpy(self, want_factors: bool = False):
+        p = self.params
+        W = np.empty(p.n1 * p.n2 * p.n3, dtype=self.dtype)
+        X = np.empty(p.n1 * p.r * p.n3, dtype=self.dtype) if want_factors else None
+        Y = np.empty(p.r * p.n2 * p.n3, dtype=self.dtype) if want_factors else None
+        self.result(W, X, Y)
+        return W, X, Y
+
+    def profile(self, n: int):
+        """Run n iterations with per-kernel CUDA events; returns the mean
+        milliseconds per launch of (xstep, ystep, slab)."""
+        ms = (ctypes.c_double * 3)()
+        _check(self._lib.tc_profile(self._ctx, int(n), ms))
+        return tuple(ms)
+
+    def close(self):
+        if self._ctx:
+            self._lib.tc_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def version() -> str:
+    return load().tc_version().decode()
