@@ -248,13 +248,16 @@ def run_ours(args):
     value = iters_total / (total_ms / 1e3)
 
     # ---- per-kernel device times (CUDA events inside the library) ------------------
-    prof = ctxs[1].profile(20)  # xstep, ystep, slab in ms
-    names = ("xstep", "ystep", "slab")
+    prof = ctxs[1].profile(20)  # qcon, xstep, ystep, slab in ms
+    names = ("qcon", "xstep", "ystep", "slab")
     s = 4
-    bytes_slab = s * N + N / 8 + 2 * s * w0.n1 * w0.n2 * S + 2 * s * (w0.n1 + w0.n2) * w0.r * S + 2 * s * w0.n1 * w0.r * S
-    bytes_y = 2 * s * w0.n1 * w0.n2 * S + 2 * s * w0.n1 * w0.r * S + 2 * 2 * s * w0.n2 * w0.r * S
-    bytes_x = 2 * s * w0.r * S * (4 * w0.n1 + w0.n2)
-    alg = {"xstep": bytes_x, "ystep": bytes_y, "slab": bytes_slab}
+    n1, n2, r = w0.n1, w0.n2, w0.r
+    rt = 2 * s * n1 * n2 * S           # one pass over the residual spectrum R~
+    fx, fy = 2 * s * r * n1 * S, 2 * s * r * n2 * S
+    alg = {"qcon": rt + fy + fx,
+           "xstep": 3 * fx + fy,
+           "ystep": rt + fx + 2 * fy,
+           "slab": s * N + N / 8 + rt + fx + fy}
     dom = names[int(np.argmax(prof))]
     peaks = {}
     try:
@@ -269,7 +272,8 @@ def run_ours(args):
                 "traffic": traffic, "kernel": dom, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg[dom],
                 "kernel_ms": {n: v for n, v in zip(names, prof)},
-                "iteration_alg_bytes": s * N + N / 8 + 4 * s * w0.n1 * w0.n2 * S}
+                "iteration_alg_bytes": sum(alg.values()),
+                "iteration_ms_sum_of_kernels": sum(prof)}
 
     # ---- recovery accuracy: FP32 vs the FP64 GPU path, 100 iterations, 20% mask ---------
     nmse = None
@@ -333,7 +337,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 3 * args.iters * args.steps, "clocks": clocks, "nmse": nmse}
+                "gpu_launches": 4 * args.iters * args.steps, "clocks": clocks, "nmse": nmse}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

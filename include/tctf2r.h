@@ -118,9 +118,11 @@ tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device)
 /* Profiling aid: run n_iters real iterations (they advance the state exactly
  * like tc_iterate) but launch the three per-iteration kernels one by one, with
  * CUDA events recorded around each on the context's stream, then synchronise.
- *   ms : receives 3 values, the mean device time per launch in milliseconds of
- *        the X-step kernel, the Y-step kernel and the slab kernel (fused
- *        synthesis / inverse DFT / W-step / forward DFT / X-contraction).
+ *   ms : receives 4 values, the mean device time per launch in milliseconds of
+ *        the four kernels of one iteration, in launch order: the X-step
+ *        contraction R~Y~^H, the X-step (with the r x r Y-step preparation),
+ *        the Y-step, and the slab kernel (synthesis / inverse DFT / W-step /
+ *        forward DFT).
  * Errors: TC_ERR_ARG (n_iters < 1 or ms NULL), TC_ERR_CUDA, TC_ERR_STATE. */
 tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
 

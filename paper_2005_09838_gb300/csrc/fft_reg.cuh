@@ -224,3 +224,30 @@ __device__ __forceinline__ void irfft(const cx<T>* X, T* x) {
 
 }  // namespace fft
 }  // namespace tc
+
+namespace tc {
+namespace fft {
+
+// Fill this translation unit's twiddle tables on the current device (FP64
+// cos/sin rounded to the table type).  Each translation unit that launches a
+// register-FFT kernel owns its own copy of the constant tables.
+template <typename T>
+static void upload_tables() {
+  cx<T> tab[kTableSize];
+  for (int i = 0; i < kNumLengths; ++i) {
+    const int L = kLengths[i];
+    const int off = table_offset(L);
+    for (int m = 0; m < L; ++m) {
+      const double a = 2.0 * 3.14159265358979323846 * (double)m / (double)L;
+      tab[off + m] = cx<T>{(T)cos(a), (T)(-sin(a))};
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    cudaMemcpyToSymbol(c_tw_f32, tab, sizeof(tab));
+  } else {
+    cudaMemcpyToSymbol(c_tw_f64, tab, sizeof(tab));
+  }
+}
+
+}  // namespace fft
+}  // namespace tc

@@ -1,0 +1,130 @@
+// Initialisation, read-back and objective helpers of the TCTF2R library (not
+// on the per-iteration path).
+#pragma once
+
+namespace tc {
+
+
+// G (column-major, i1 fastest) and the byte mask -> internal row layout and
+// mask bits.  One CTA per (i1, i3) row.
+template <typename T>
+__global__ void k_pack(const T* __restrict__ Gin, const uint8_t* __restrict__ Min, T* __restrict__ Gout,
+                       uint32_t* __restrict__ Mout, int n1, int n2, int n3, int words) {
+  const int row = blockIdx.x;  // i1 * n3 + i3
+  const int i1 = row / n3, i3 = row - i1 * n3;
+  for (int j0 = 0; j0 < words * 32; j0 += blockDim.x) {
+    const int j = j0 + threadIdx.x;
+    bool obs = false;
+    T g = T(0);
+    if (j < n2) {
+      const size_t src = (size_t)i1 + (size_t)n1 * ((size_t)j + (size_t)n2 * i3);
+      obs = Min[src] != 0;
+      g = obs ? Gin[src] : T(0);
+      Gout[(size_t)row * n2 + j] = g;
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, obs);
+    if ((threadIdx.x & 31) == 0 && j < words * 32) Mout[(size_t)row * words + (j >> 5)] = bits;
+  }
+}
+
+// Direct DFT (Eq. (bar BA-k), forward sign convention of the library) of a
+// real factor along mode 3, written to the half spectrum [S][r][n]:
+//   transposed = 0: input n x r x n3 (X0: i fastest, then s)
+//   transposed = 1: input r x n x n3 (Y0: s fastest, then i)
+template <typename T>
+__global__ void k_factor_dft(const T* __restrict__ in, cx<T>* __restrict__ out, int n, int r, int n3, int transposed) {
+  const int S = n3 / 2 + 1;
+  const size_t total = (size_t)S * r * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const int s = (int)((e / n) % r);
+    const int k = (int)(e / ((size_t)n * r));
+    double re = 0.0, im = 0.0;
+    for (int l = 0; l < n3; ++l) {
+      const size_t src = transposed ? ((size_t)s + (size_t)r * ((size_t)i + (size_t)n * l))
+                                    : ((size_t)i + (size_t)n * ((size_t)s + (size_t)r * l));
+      const double v = (double)in[src];
+      double sn, cs;
+      sincospi(2.0 * (double)((long long)k * l % n3) / (double)n3, &sn, &cs);
+      re += v * cs;
+      im -= v * sn;
+    }
+    if (k == 0 || 2 * k == n3) im = 0.0;
+    out[e] = cx<T>{(T)re, (T)im};
+  }
+}
+
+// Inverse of k_factor_dft (Eq. (barAAk)) back to the caller's layout.
+template <typename T>
+__global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out, int n, int r, int n3, int transposed) {
+  const int S = n3 / 2 + 1;
+  const bool even = (n3 % 2) == 0;
+  const int kmax = even ? S - 2 : S - 1;
+  const size_t total = (size_t)n * r * n3;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    int i, s, l;
+    if (transposed) {
+      s = (int)(e % r);
+      i = (int)((e / r) % n);
+      l = (int)(e / ((size_t)r * n));
+    } else {
+      i = (int)(e % n);
+      s = (int)((e / n) % r);
+      l = (int)(e / ((size_t)n * r));
+    }
+    double acc = (double)in[((size_t)0 * r + s) * n + i].re;
+    for (int k = 1; k <= kmax; ++k) {
+      const cx<T> v = in[((size_t)k * r + s) * n + i];
+      double sn, cs;
+      sincospi(2.0 * (double)((long long)k * l % n3) / (double)n3, &sn, &cs);
+      // 2 Re(v * exp(+i theta))
+      acc += 2.0 * ((double)v.re * cs - (double)v.im * sn);
+    }
+    if (even) {
+      const double nyq = (double)in[((size_t)(S - 1) * r + s) * n + i].re;
+      acc += (l & 1) ? -nyq : nyq;
+    }
+    out[e] = (T)(acc / (double)n3);
+  }
+}
+
+// rho1 term of f0 per slice: tr((X~^H H^T H X~)(Y~ Y~^H)) in FP64.
+template <typename T>
+__global__ void k_rho1_term(Dev<T> d) {
+  __shared__ double part[32];
+  const int k = blockIdx.x;
+  const int n1 = d.n1, n2 = d.n2, r = d.r;
+  const cx<T>* X = d.Xt + (size_t)k * r * n1;
+  const cx<T>* Y = d.Yt + (size_t)k * r * n2;
+  double tot = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int s = e / r, u = e - s * r;
+    double hre = 0.0, him = 0.0;  // (HX)^H (HX) [s][u]
+    for (int i = 0; i + 1 < n1; ++i) {
+      const cx<T> a0 = X[(size_t)s * n1 + i], a1 = X[(size_t)s * n1 + i + 1];
+      const cx<T> b0 = X[(size_t)u * n1 + i], b1 = X[(size_t)u * n1 + i + 1];
+      const double ar = (double)a0.re - (double)a1.re, ai = (double)a0.im - (double)a1.im;
+      const double br = (double)b0.re - (double)b1.re, bi = (double)b0.im - (double)b1.im;
+      hre += ar * br + ai * bi;
+      him += ar * bi - ai * br;
+    }
+    double yre = 0.0, yim = 0.0;  // (Y Y^H)[u][s]
+    for (int j = 0; j < n2; ++j) {
+      const cx<T> a = Y[(size_t)u * n2 + j], b = Y[(size_t)s * n2 + j];
+      yre += (double)a.re * (double)b.re + (double)a.im * (double)b.im;
+      yim += (double)a.im * (double)b.re - (double)a.re * (double)b.im;
+    }
+    tot += hre * yre - him * yim;
+  }
+  tot = warp_sum(tot);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) part[wid] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    d.part_k[k] = s;
+  }
+}
+
+}  // namespace tc

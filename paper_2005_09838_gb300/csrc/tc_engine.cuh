@@ -1,5 +1,5 @@
 // Host engine of one precision: owns the device state of a context, launches
-// the kernels of tc_kernels.cuh and captures one iteration as a CUDA graph.
+// the kernels and captures one iteration (four kernels) as a CUDA graph.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,36 +26,53 @@ namespace tc {
   } while (0)
 
 template <typename T>
-using SlabFn = void (*)(Dev<T>, T*, int);
+using SlabFn = void (*)(Dev<T>, T*, int, int);
 
-// Slab-kernel instances per specialised tube length (L = 0: generic).
 template <typename T, int L>
-inline void slab_table(SlabFn<T> f[4]) {
+inline void slab_table(SlabFn<T> f[3]) {
   f[MODE_ITER] = k_slab<T, L, MODE_ITER>;
-  f[MODE_INIT] = k_slab<T, L, MODE_INIT>;
   f[MODE_W] = k_slab<T, L, MODE_W>;
   f[MODE_R] = k_slab<T, L, MODE_R>;
 }
 
-// Which register-FFT lengths each precision instantiates.
+// Register-FFT lengths instantiated per precision (defined per translation unit).
 template <typename T>
-bool pick_slab(int n3, SlabFn<T> f[4]);
+bool pick_slab(int n3, SlabFn<T> f[3]);
 
 template <typename T>
 using YFn = void (*)(Dev<T>);
+template <typename T>
+using QFn = void (*)(Dev<T>, cx<T>*);
 
 template <typename T>
-inline YFn<T> pick_ystep(int r, int* rp) {
-  if (r <= 2) { *rp = 2; return k_ystep<T, 2>; }
-  if (r <= 4) { *rp = 4; return k_ystep<T, 4>; }
-  if (r <= 8) { *rp = 8; return k_ystep<T, 8>; }
-  if (r <= 16) { *rp = 16; return k_ystep<T, 16>; }
-  *rp = 32;
-  return k_ystep<T, 32>;
+inline int pad_rank(int r) {
+  return r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : r <= 16 ? 16 : 32;
 }
 
 template <typename T>
-void upload_twiddles(cudaStream_t s);
+inline YFn<T> pick_ystep(int rp) {
+  switch (rp) {
+    case 2: return k_ystep<T, 2>;
+    case 4: return k_ystep<T, 4>;
+    case 8: return k_ystep<T, 8>;
+    case 16: return k_ystep<T, 16>;
+    default: return k_ystep<T, 32>;
+  }
+}
+
+template <typename T>
+inline QFn<T> pick_qcon(int rp) {
+  switch (rp) {
+    case 2: return k_qcon<T, 2>;
+    case 4: return k_qcon<T, 4>;
+    case 8: return k_qcon<T, 8>;
+    case 16: return k_qcon<T, 16>;
+    default: return k_qcon<T, 32>;
+  }
+}
+
+template <typename T>
+void upload_twiddles();
 
 template <typename T>
 class Engine final : public EngineBase {
@@ -81,32 +98,35 @@ class Engine final : public EngineBase {
     r_ = p.r;
     S_ = n3_ / 2 + 1;
     words_ = (n2_ + 31) / 32;
+    rp_ = pad_rank<T>(r_);
     const size_t N = (size_t)n1_ * n2_ * n3_;
     TC_CUDA_TRY(cudaGetDevice(&device_));
     int optin = 0;
     TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device_));
-    upload_twiddles<T>(stream_);
+    upload_twiddles<T>();
     TC_CUDA_TRY(cudaGetLastError());
 
-    // ---- state buffers ---------------------------------------------------------
+    // ---- state buffers -----------------------------------------------------------
+    const size_t nx = (size_t)S_ * r_ * n1_, ny = (size_t)S_ * r_ * n2_, nrr = (size_t)S_ * r_ * r_;
     T* Gint = alloc<T>(N, err);
     uint32_t* maskbits = alloc<uint32_t>((size_t)n1_ * n3_ * words_, err);
     cx<T>* Rt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
-    cx<T>* Xt = alloc<cx<T>>((size_t)S_ * r_ * n1_, err);
-    cx<T>* Q = alloc<cx<T>>((size_t)S_ * r_ * n1_, err);
-    cx<T>* Tb = alloc<cx<T>>((size_t)S_ * r_ * n1_, err);
-    cx<T>* Yt = alloc<cx<T>>((size_t)S_ * r_ * n2_, err);
-    cx<T>* Mm = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
-    cx<T>* Gp = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
-    T* winv = alloc<T>((size_t)2 * n2_, err);
-    T* hinv = alloc<T>((size_t)n1_, err);
+    cx<T>* Xt = alloc<cx<T>>(nx, err);
+    Q_ = alloc<cx<T>>(nx, err);
+    cx<T>* Tb = alloc<cx<T>>(nx, err);
+    cx<T>* Yt = alloc<cx<T>>(ny, err);
+    cx<T>* Mm = alloc<cx<T>>(nrr, err);
+    cx<T>* Gp = alloc<cx<T>>(nrr, err);
+    cx<T>* Gplo = alloc<cx<T>>(nrr, err);
+    T* winv = alloc<T>((size_t)4 * n2_, err);
+    T* hinv = alloc<T>((size_t)2 * n1_, err);
     cx<T>* twg = alloc<cx<T>>((size_t)n3_, err);
     double* part = alloc<double>((size_t)n1_ * 4, err);
     double* part_k = alloc<double>((size_t)S_, err);
     int* derr = alloc<int>(1, err);
     if (!err.empty()) return TC_ERR_NOMEM;
 
-    // ---- slab kernel choice and shared memory -------------------------------------
+    // ---- kernel variants and shared memory -------------------------------------------
     specialised_ = pick_slab<T>(n3_, slab_) && ((n2_ + 31) / 32 * 32 <= kSlabMaxThreads);
     if (!specialised_) slab_table<T, 0>(slab_);
     slab_threads_ = specialised_ ? (n2_ + 31) / 32 * 32 : 256;
@@ -121,39 +141,56 @@ class Engine final : public EngineBase {
       d_.scratch = nullptr;
     }
     slab_smem_ = lay.total;
-    for (int m = 0; m < 4; ++m)
+    for (int m = 0; m < 3; ++m)
       TC_CUDA_TRY(cudaFuncSetAttribute(slab_[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab_smem_));
-    xstep_smem_ = xstep_smem_bytes<T>(r_);
-    TC_CUDA_TRY(cudaFuncSetAttribute(k_xstep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xstep_smem_));
-    ystep_ = pick_ystep<T>(r_, &rp_);
-    ystep_smem_ = (size_t)(kYThreads / 32 + 2) * rp_ * 32 * sizeof(cx<T>);
-    TC_CUDA_TRY(cudaFuncSetAttribute(ystep_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ystep_smem_));
 
-    // ---- host tables (FP64, rounded to T) -------------------------------------------
+    XLayout xl = xstep_layout<T>(n1_, n2_, r_, true);
+    xarrays_in_smem_ = xl.total <= (size_t)optin;
+    if (!xarrays_in_smem_) xl = xstep_layout<T>(n1_, n2_, r_, false);
+    xstep_smem_ = xl.total;
+    if (xstep_smem_ > (size_t)optin) {
+      err = "X-step shared memory exceeds the device limit";
+      return TC_ERR_UNSUPPORTED;
+    }
+    TC_CUDA_TRY(cudaFuncSetAttribute(k_xstep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xstep_smem_));
+    ystep_ = pick_ystep<T>(rp_);
+    ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
+    qcon_ = pick_qcon<T>(rp_);
+    qcon_smem_ = qcon_smem_bytes<T>(n2_, r_, rp_);
+    if (ystep_smem_ > (size_t)optin || qcon_smem_ > (size_t)optin) {
+      err = "shared memory of the slice kernels exceeds the device limit for these sizes";
+      return TC_ERR_UNSUPPORTED;
+    }
+    TC_CUDA_TRY(cudaFuncSetAttribute(ystep_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ystep_smem_));
+    TC_CUDA_TRY(cudaFuncSetAttribute(qcon_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qcon_smem_));
+
+    // ---- host tables (FP64, rounded to T) ----------------------------------------------
     {
       const double mu = p.mu, rho1 = p.rho1, rho2 = p.rho2;
-      std::vector<T> w(2 * (size_t)n2_);
-      // runs starting at j = 0 (first entry has one neighbour when n2 > 1)
+      // W-step runs: inverse LU pivots by position in the run; runs starting at
+      // j = 0 have one neighbour at their first entry (when n2 > 1)
+      std::vector<T> w(4 * (size_t)n2_);
       double inv = 1.0 / (1.0 + mu + rho2 * (n2_ > 1 ? 1.0 : 0.0));
-      w[0] = (T)inv;
-      for (int q = 1; q < n2_; ++q) {
-        inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
+      for (int q = 0; q < n2_; ++q) {
+        if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
         w[q] = (T)inv;
+        w[2 * n2_ + q] = (T)(rho2 * inv);
       }
       inv = 1.0 / (1.0 + mu + 2.0 * rho2);
-      w[n2_] = (T)inv;
-      for (int q = 1; q < n2_; ++q) {
-        inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
+      for (int q = 0; q < n2_; ++q) {
+        if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
         w[n2_ + q] = (T)inv;
+        w[3 * n2_ + q] = (T)(rho2 * inv);
       }
-      std::vector<T> h(n1_);
       // H_rho1 = I + rho1 H^T H: diagonal 1 + rho1 deg_i, off-diagonal -rho1
+      std::vector<T> h(2 * (size_t)n1_);
       double hi = 0.0;
       for (int i = 0; i < n1_; ++i) {
         const int deg = (i > 0) + (i + 1 < n1_);
         const double den = 1.0 + rho1 * deg - (i > 0 ? rho1 * rho1 * hi : 0.0);
         hi = 1.0 / den;
         h[i] = (T)hi;
+        h[n1_ + i] = (T)(rho1 * hi);
       }
       std::vector<cx<T>> tw(n3_);
       for (int m = 0; m < n3_; ++m) {
@@ -163,7 +200,7 @@ class Engine final : public EngineBase {
       TC_CUDA_TRY(cudaMemcpyAsync(winv, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
       TC_CUDA_TRY(cudaMemcpyAsync(hinv, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
       TC_CUDA_TRY(cudaMemcpyAsync(twg, tw.data(), tw.size() * sizeof(cx<T>), cudaMemcpyHostToDevice, stream_));
-      TC_CUDA_TRY(cudaStreamSynchronize(stream_));  // host vectors go out of scope
+      TC_CUDA_TRY(cudaStreamSynchronize(stream_));  // the host vectors go out of scope
     }
 
     d_.n1 = n1_;
@@ -180,10 +217,10 @@ class Engine final : public EngineBase {
     d_.Rt = Rt;
     d_.Xt = Xt;
     d_.Yt = Yt;
-    d_.Q = Q;
-    d_.Tb = Tb;
     d_.Mm = Mm;
     d_.Gp = Gp;
+    d_.Gplo = Gplo;
+    d_.Tb = Tb;
     d_.winv = winv;
     d_.hinv = hinv;
     d_.twg = twg;
@@ -191,10 +228,9 @@ class Engine final : public EngineBase {
     d_.part_k = part_k;
     d_.err = derr;
     d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * 2.220446049250313e-16;
-    d_.pinv_fallbacks_enabled = 1;
     TC_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), stream_));
 
-    // ---- inputs ------------------------------------------------------------------------
+    // ---- inputs --------------------------------------------------------------------------
     const T* dG = static_cast<const T*>(G);
     const uint8_t* dM = mask;
     const T* dY = static_cast<const T*>(Y0);
@@ -213,6 +249,7 @@ class Engine final : public EngineBase {
       dY = static_cast<const T*>(stage(Y0, (size_t)r_ * n2_ * n3_ * sizeof(T)));
       dX = X0 ? static_cast<const T*>(stage(X0, (size_t)n1_ * r_ * n3_ * sizeof(T))) : nullptr;
       if (!dG || !dM || !dY || (X0 && !dX)) {
+        cudaStreamSynchronize(stream_);
         for (void* q : tmp) cudaFree(q);
         err = "staging of host inputs failed";
         return TC_ERR_NOMEM;
@@ -224,9 +261,9 @@ class Engine final : public EngineBase {
     if (dX) {
       k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dX, Xt, n1_, r_, n3_, 0);
     } else {
-      cudaMemsetAsync(Xt, 0, (size_t)S_ * r_ * n1_ * sizeof(cx<T>), stream_);
+      cudaMemsetAsync(Xt, 0, nx * sizeof(cx<T>), stream_);
     }
-    launch_slab(MODE_INIT, nullptr, stream_);
+    launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - X0*Y0)
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(stream_);
     for (void* q : tmp) cudaFree(q);
@@ -257,8 +294,8 @@ class Engine final : public EngineBase {
       err = "context poisoned by an earlier error";
       return TC_ERR_STATE;
     }
-    launch_slab(MODE_R, nullptr, stream_);
-    launch_slab(MODE_W, nullptr, stream_);
+    launch_slab(MODE_R, nullptr, 0, stream_);
+    launch_slab(MODE_W, nullptr, 0, stream_);
     k_rho1_term<T><<<S_, 256, 0, stream_>>>(d_);
     TC_CUDA_TRY(cudaGetLastError());
     std::vector<double> part((size_t)n1_ * 4), pk(S_);
@@ -278,6 +315,8 @@ class Engine final : public EngineBase {
       const double c = (k == 0 || 2 * k == n3_) ? 1.0 : 2.0;
       sh += c * pk[k];
     }
+    // f0 of Eq. (TETP-optim): ||Z - W||^2 = ||R||^2; the rho1 term by Parseval
+    // from the factors (Eq. (HunfZ2))
     const double f = 0.5 * sr + 0.5 * p_.mu * sw + 0.5 * p_.rho2 * sk + 0.5 * p_.rho1 * sh / (double)n3_;
     *f0 = f;
     if (resid_obs) *resid_obs = std::sqrt(so);
@@ -295,9 +334,6 @@ class Engine final : public EngineBase {
     }
     const size_t N = (size_t)n1_ * n2_ * n3_;
     const size_t nx = (size_t)n1_ * r_ * n3_, ny = (size_t)r_ * n2_ * n3_;
-    T* dW = nullptr;
-    T* dXo = nullptr;
-    T* dYo = nullptr;
     std::vector<void*> tmp;
     auto dev_buf = [&](void* user, size_t elems) -> T* {
       if (!user) return nullptr;
@@ -307,15 +343,15 @@ class Engine final : public EngineBase {
       tmp.push_back(q);
       return static_cast<T*>(q);
     };
-    dW = dev_buf(W, N);
-    dXo = dev_buf(X, nx);
-    dYo = dev_buf(Y, ny);
+    T* dW = dev_buf(W, N);
+    T* dXo = dev_buf(X, nx);
+    T* dYo = dev_buf(Y, ny);
     if ((W && !dW) || (X && !dXo) || (Y && !dYo)) {
       for (void* q : tmp) cudaFree(q);
       err = "allocation of read-back buffers failed";
       return TC_ERR_NOMEM;
     }
-    if (dW) launch_slab(MODE_W, dW, stream_);
+    if (dW) launch_slab(MODE_W, dW, 0, stream_);
     const int fgrid = 4 * 152;
     if (dXo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Xt, dXo, n1_, r_, n3_, 0);
     if (dYo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Yt, dYo, n2_, r_, n3_, 1);
@@ -340,34 +376,36 @@ class Engine final : public EngineBase {
       err = "context poisoned by an earlier error";
       return TC_ERR_STATE;
     }
-    cudaEvent_t ev[4];
-    for (int i = 0; i < 4; ++i) TC_CUDA_TRY(cudaEventCreate(&ev[i]));
-    double acc[3] = {0, 0, 0};
+    constexpr int K = 4;
+    cudaEvent_t ev[K + 1];
+    for (int i = 0; i <= K; ++i) TC_CUDA_TRY(cudaEventCreate(&ev[i]));
+    double acc[K] = {0, 0, 0, 0};
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < n && e == cudaSuccess; ++it) {
       cudaEventRecord(ev[0], stream_);
-      k_xstep<T><<<S_, kSliceThreads, xstep_smem_, stream_>>>(d_);
+      launch_qcon(stream_);
       cudaEventRecord(ev[1], stream_);
-      dim3 yg(S_, (n2_ + 31) / 32);
-      ystep_<<<yg, kYThreads, ystep_smem_, stream_>>>(d_);
+      launch_xstep(stream_);
       cudaEventRecord(ev[2], stream_);
-      launch_slab(MODE_ITER, nullptr, stream_);
+      launch_ystep(stream_);
       cudaEventRecord(ev[3], stream_);
+      launch_slab(MODE_ITER, nullptr, 0, stream_);
+      cudaEventRecord(ev[4], stream_);
       e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-      for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
+      for (int q = 0; q < K && e == cudaSuccess; ++q) {
         float t = 0.f;
         e = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
         acc[q] += t;
       }
     }
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i <= K; ++i) cudaEventDestroy(ev[i]);
     if (e != cudaSuccess) {
       err = std::string("profiled iteration failed: ") + cudaGetErrorString(e);
       poisoned_ = true;
       return TC_ERR_CUDA;
     }
-    for (int q = 0; q < 3; ++q) ms[q] = acc[q] / n;
+    for (int q = 0; q < K; ++q) ms[q] = acc[q] / n;
     return check_dev_err(err);
   }
 
@@ -386,15 +424,28 @@ class Engine final : public EngineBase {
     return static_cast<U*>(q);
   }
 
-  void launch_slab(int mode, T* Wout, cudaStream_t s) {
-    slab_[mode]<<<n1_, slab_threads_, slab_smem_, s>>>(d_, Wout, slabs_in_smem_ ? 1 : 0);
+  void launch_slab(int mode, T* Wout, int init, cudaStream_t s) {
+    slab_[mode]<<<n1_, slab_threads_, slab_smem_, s>>>(d_, Wout, slabs_in_smem_ ? 1 : 0, init);
+  }
+  void launch_qcon(cudaStream_t s) {
+    dim3 g(S_, (n1_ + 31) / 32);
+    qcon_<<<g, kSliceThreads, qcon_smem_, s>>>(d_, Q_);
+  }
+  void launch_xstep(cudaStream_t s) {
+    k_xstep<T><<<S_, kSliceThreads, xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
+  }
+  void launch_ystep(cudaStream_t s) {
+    dim3 g(S_, (n2_ + 31) / 32);
+    ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
   }
 
+  // One TCTF2R iteration: Q = R~Y~^H, X-step (+ Y-step r x r work), Y-step,
+  // then the slab kernel (Z, W-step, R~).
   void launch_iteration(cudaStream_t s) {
-    k_xstep<T><<<S_, kSliceThreads, xstep_smem_, s>>>(d_);
-    dim3 yg(S_, (n2_ + 31) / 32);
-    ystep_<<<yg, kYThreads, ystep_smem_, s>>>(d_);
-    launch_slab(MODE_ITER, nullptr, s);
+    launch_qcon(s);
+    launch_xstep(s);
+    launch_ystep(s);
+    launch_slab(MODE_ITER, nullptr, 0, s);
   }
 
   tc_status capture(std::string& err) {
@@ -437,15 +488,17 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr;
   cudaGraphExec_t graph_exec_ = nullptr;
   int device_ = 0;
-  int n1_ = 0, n2_ = 0, n3_ = 0, r_ = 0, S_ = 0, words_ = 0;
+  int n1_ = 0, n2_ = 0, n3_ = 0, r_ = 0, S_ = 0, words_ = 0, rp_ = 8;
   bool poisoned_ = false;
   bool specialised_ = false;
   bool slabs_in_smem_ = true;
+  bool xarrays_in_smem_ = true;
   int slab_threads_ = 256;
-  size_t slab_smem_ = 0, xstep_smem_ = 0, ystep_smem_ = 0;
-  int rp_ = 8;
-  SlabFn<T> slab_[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t slab_smem_ = 0, xstep_smem_ = 0, ystep_smem_ = 0, qcon_smem_ = 0;
+  SlabFn<T> slab_[3] = {nullptr, nullptr, nullptr};
   YFn<T> ystep_ = nullptr;
+  QFn<T> qcon_ = nullptr;
+  cx<T>* Q_ = nullptr;
   Dev<T> d_{};
   std::vector<void*> allocs_;
 };

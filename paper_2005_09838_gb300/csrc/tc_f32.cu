@@ -1,34 +1,23 @@
-// float instantiation of the TCTF2R engine.
-#include <cmath>
-#include <vector>
-
+// FP32 engine: generic slab kernel here; the register-FFT slab kernels live in
+// their own translation units (compiled in parallel).
 #include "tc_engine.cuh"
 
 namespace tc {
 
+bool slab_setup_f32_112(SlabFn<float> f[3]);
+bool slab_setup_f32_168(SlabFn<float> f[3]);
+
 template <>
-bool pick_slab<float>(int n3, SlabFn<float> f[4]) {
+bool pick_slab<float>(int n3, SlabFn<float> f[3]) {
   switch (n3) {
-    case 112: slab_table<float, 112>(f); return true;
-    case 168: slab_table<float, 168>(f); return true;
-    default:
-      return false;
+    case 112: return slab_setup_f32_112(f);
+    case 168: return slab_setup_f32_168(f);
+    default: return false;
   }
 }
 
 template <>
-void upload_twiddles<float>(cudaStream_t) {
-  std::vector<cx<float>> tab(fft::kTableSize);
-  for (int i = 0; i < fft::kNumLengths; ++i) {
-    const int L = fft::kLengths[i];
-    const int off = fft::table_offset(L);
-    for (int m = 0; m < L; ++m) {
-      const double a = 2.0 * M_PI * (double)m / (double)L;
-      tab[off + m] = cx<float>{(float)std::cos(a), (float)(-std::sin(a))};
-    }
-  }
-  cudaMemcpyToSymbol(fft::c_tw_f32, tab.data(), tab.size() * sizeof(cx<float>));
-}
+void upload_twiddles<float>() {}
 
 EngineBase* make_engine_f32() { return new Engine<float>(); }
 

@@ -147,8 +147,8 @@ class Completion:
 
     def profile(self, n: int):
         """Run n iterations with per-kernel CUDA events; returns the mean
-        milliseconds per launch of (xstep, ystep, slab)."""
-        ms = (ctypes.c_double * 3)()
+        milliseconds per launch of (qcon, xstep, ystep, slab)."""
+        ms = (ctypes.c_double * 4)()
         _check(self._lib.tc_profile(self._ctx, int(n), ms))
         return tuple(ms)
 
