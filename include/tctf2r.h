@@ -126,6 +126,31 @@ tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device)
  * Errors: TC_ERR_ARG (n_iters < 1 or ms NULL), TC_ERR_CUDA, TC_ERR_STATE. */
 tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
 
+/* Allocation-free completion of a small tensor (this entry point has no
+ * counterpart in the paper; it is a deployment aid).  Some callers cannot call
+ * cudaMalloc: code hosted in a framework whose allocator owns the device
+ * memory, and latency-critical loops in which cudaMalloc/cudaFree could
+ * synchronise the device and stall other streams.  tc_complete_static runs the
+ * same computation as tc_init + tc_iterate(n_iters) + tc_result(W) (+
+ * tc_objective) without allocating anything: every intermediate array lives in
+ * one file-scope device array of 16 MiB, which every GPU that loads the library
+ * holds until the process exits.
+ *   p       : parameters (exact steps, eps = 0)
+ *   G, mask, Y0, X0 : DEVICE pointers on the current device, layouts as for
+ *             tc_init (X0 may be NULL); W : DEVICE output, n1*n2*n3 reals
+ *   f0      : host pointer receiving f0 of the final iterate, or NULL
+ *   cuda_stream : stream to run on; the call synchronises it before returning
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; the call
+ * clears what must start at zero.  Calls that overlap on the GPU (other host
+ * threads or streams) race on the array and must be serialised by the caller.
+ * Errors: TC_ERR_ARG for bad arguments or a problem whose arrays exceed the
+ * 16 MiB scratch (the message gives the bytes needed), TC_ERR_UNSUPPORTED,
+ * TC_ERR_CUDA, TC_ERR_NUMERIC. */
+tc_status tc_complete_static(const tc_params* p, const void* G, const uint8_t* mask, const void* Y0,
+                             const void* X0, int32_t n_iters, void* W, double* f0, void* cuda_stream);
+
 /* Release a context and its device memory.  NULL-safe.  Synchronises the
  * context's stream first. */
 tc_status tc_free(tc_ctx* c);

@@ -52,6 +52,11 @@ tc_status validate(const tc_params* p) {
 
 }  // namespace
 
+namespace tc {
+// Lets other translation units of the library report through tc_last_error().
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace tc
+
 extern "C" {
 
 const char* tc_last_error(void) { return g_last_error.c_str(); }

@@ -72,6 +72,9 @@ def load(path: str | None = None):
     lib.tc_result.restype = ctypes.c_int
     lib.tc_profile.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     lib.tc_profile.restype = ctypes.c_int
+    lib.tc_complete_static.argtypes = [ctypes.POINTER(tc_params), P, P, P, P, ctypes.c_int32, P,
+                                       ctypes.POINTER(ctypes.c_double), P]
+    lib.tc_complete_static.restype = ctypes.c_int
     lib.tc_free.argtypes = [P]
     lib.tc_free.restype = ctypes.c_int
     lib.tc_last_error.argtypes = []
@@ -168,6 +171,20 @@ class Completion:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def complete_static(params: tc_params, G, mask, Y0, n_iters: int, W, X0=None, stream: int | None = None,
+                    want_f0: bool = True):
+    """tc_complete_static: the whole completion with no device allocation, for
+    callers that cannot call cudaMalloc (their device memory belongs to a host
+    framework's allocator, or a cudaMalloc would stall a latency-critical
+    loop).  All buffers are device tensors; returns f0 (or None)."""
+    lib = load()
+    f0 = ctypes.c_double()
+    st = lib.tc_complete_static(ctypes.byref(params), _ptr(G), _ptr(mask), _ptr(Y0), _ptr(X0), int(n_iters), _ptr(W),
+                                ctypes.byref(f0) if want_f0 else None, stream)
+    _check(st)
+    return f0.value if want_f0 else None
 
 
 def version() -> str:
