@@ -252,12 +252,14 @@ def run_ours(args):
     names = ("qcon", "xstep", "ystep", "slab")
     s = 4
     n1, n2, r = w0.n1, w0.n2, w0.r
-    rt = 2 * s * n1 * n2 * S           # one pass over the residual spectrum R~
+    rt = 2 * s * n1 * n2 * S           # one pass over a half spectrum of the slab (R~ or Z~)
     fx, fy = 2 * s * r * n1 * S, 2 * s * r * n2 * S
-    alg = {"qcon": rt + fy + fx,
-           "xstep": 3 * fx + fy,
-           "ystep": rt + fx + 2 * fy,
-           "slab": s * N + N / 8 + rt + fx + fy}
+    ag = 16 * S * ((n2 + 31) // 32) * (r * (r + 1) // 2)   # FP64 tile Grams of Y~
+    maskb = 4 * n1 * n2 * ((w0.n3 + 31) // 32)              # mask words
+    alg = {"qcon": rt + fy + fx,                 # R~, Y~ in; Q out
+           "xstep": 3 * fx + ag,                 # X~, Q in; X~' out; tile Grams in
+           "ystep": 2 * rt + fx + 2 * fy + ag,   # R~, X~', Y~ in; Y~', Z~, tile Grams out
+           "slab": s * N + maskb + 2 * rt}       # G, mask, Z~ in; R~ out
     dom = names[int(np.argmax(prof))]
     peaks = {}
     try:

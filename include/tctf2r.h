@@ -69,7 +69,8 @@ typedef struct {
   double alpha, beta;  /* step sizes, used only with TC_STEP_SCALED, > 0 */
   double eps;          /* stopping tolerance of step 6; 0 = run exactly n iterations */
   double pinv_rtol;    /* Gram eigenvalues <= pinv_rtol * lambda_max are cut by the
-                          pseudo-inverse; <= 0 selects r * 2^-52 */
+                          pseudo-inverse; <= 0 selects r times the machine epsilon
+                          of the working precision (2^-52 FP64, 2^-23 FP32) */
 } tc_params;
 
 typedef struct tc_ctx tc_ctx;

@@ -5,25 +5,25 @@
 namespace tc {
 
 
-// G (column-major, i1 fastest) and the byte mask -> internal row layout and
-// mask bits.  One CTA per (i1, i3) row.
+// G (column-major, i1 fastest) and the byte mask -> the internal layouts:
+// G row-major [i1][i3][i2] (coalesced for tube-per-thread loads) and mask
+// words tube-major [i1][i2][ceil(n3/32)] (bit i3 % 32 of word i3 / 32).  One
+// CTA per tube (i1, i2).
 template <typename T>
 __global__ void k_pack(const T* __restrict__ Gin, const uint8_t* __restrict__ Min, T* __restrict__ Gout,
                        uint32_t* __restrict__ Mout, int n1, int n2, int n3, int words) {
-  const int row = blockIdx.x;  // i1 * n3 + i3
-  const int i1 = row / n3, i3 = row - i1 * n3;
-  for (int j0 = 0; j0 < words * 32; j0 += blockDim.x) {
-    const int j = j0 + threadIdx.x;
+  const int tube = blockIdx.x;  // i1 * n2 + i2
+  const int i1 = tube / n2, i2 = tube - i1 * n2;
+  for (int l0 = 0; l0 < words * 32; l0 += blockDim.x) {
+    const int l = l0 + threadIdx.x;
     bool obs = false;
-    T g = T(0);
-    if (j < n2) {
-      const size_t src = (size_t)i1 + (size_t)n1 * ((size_t)j + (size_t)n2 * i3);
+    if (l < n3) {
+      const size_t src = (size_t)i1 + (size_t)n1 * ((size_t)i2 + (size_t)n2 * l);
       obs = Min[src] != 0;
-      g = obs ? Gin[src] : T(0);
-      Gout[(size_t)row * n2 + j] = g;
+      Gout[((size_t)i1 * n3 + l) * n2 + i2] = obs ? Gin[src] : T(0);
     }
     const unsigned bits = __ballot_sync(0xffffffffu, obs);
-    if ((threadIdx.x & 31) == 0 && j < words * 32) Mout[(size_t)row * words + (j >> 5)] = bits;
+    if ((threadIdx.x & 31) == 0 && l < words * 32) Mout[(size_t)tube * words + (l >> 5)] = bits;
   }
 }
 
@@ -124,6 +124,45 @@ __global__ void k_rho1_term(Dev<T> d) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
     d.part_k[k] = s;
+  }
+}
+
+}  // namespace tc
+
+namespace tc {
+
+// Initial Z~ = X~Y~ (step 3 at the initial point; during the iteration the
+// Y-step kernel writes Z~).  One thread per output.
+template <typename T>
+__global__ void k_synth_init(Dev<T> d) {
+  const size_t total = (size_t)d.n1 * d.S * d.n2;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e % d.n2);
+    const int k = (int)((e / d.n2) % d.S);
+    const int i = (int)(e / ((size_t)d.n2 * d.S));
+    cx<T> z = {T(0), T(0)};
+    for (int s = 0; s < d.r; ++s)
+      cfma(z, d.Xt[((size_t)k * d.r + s) * d.n1 + i], d.Yt[((size_t)k * d.r + s) * d.n2 + j]);
+    d.Zt[e] = z;
+  }
+}
+
+// Initial tile Grams of Y~ (the X-step's A for the first iteration).  Grid
+// (S, ytiles), one warp per upper-triangle entry.
+template <typename T>
+__global__ void k_gram_tiles(Dev<T> d) {
+  const int k = blockIdx.x, tile = blockIdx.y;
+  const int r = d.r, n2 = d.n2, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ntask = r * (r + 1) / 2;
+  const int j = tile * 32 + lane;
+  for (int task = wid; task < ntask; task += nw) {
+    int s, u;
+    tri_index(task, r, s, u);
+    cx<T> g = {T(0), T(0)};  // the same arithmetic as the tile Grams of k_ystep
+    if (j < n2) cfmac(g, d.Yt[((size_t)k * r + s) * n2 + j], d.Yt[((size_t)k * r + u) * n2 + j]);
+    g.re = warp_sum(g.re);
+    g.im = warp_sum(g.im);
+    if (lane == 0) d.Ag[((size_t)k * d.ytiles + tile) * ntask + task] = cx<double>{(double)g.re, (double)g.im};
   }
 }
 

@@ -1,12 +1,13 @@
 // Slab kernel of the TCTF2R iteration: one CTA per mode-1 index i1 (one OD
-// pair), holding the spatial slab (i1, :, :) in shared memory.
+// pair).  The spatial slab (i1, :, :) lives in shared memory, tube-major with
+// an odd stride (conflict-free for tube-per-thread and row-per-thread access).
 //
-//   phase A  Z~(i1, j, k) = sum_s X~(i1, s, k) Y~(s, j, k) for the solved
-//            slices k (step 3), inverse mode-3 DFT of every tube (Eq. (barAAk))
-//   phase B  W-step of every row (i1, :, i3) (step 4, Eq. (subquKKT)), written
-//            as the residual R = W - Z
-//   phase C  forward mode-3 DFT of every tube of R (step 7, Eq. (bar BA-k)),
-//            stored as R~
+//   phase A  inverse mode-3 DFT (Eq. (barAAk)) of every tube of Z~ = X~Y~
+//            (step 3; the half spectrum is written by the Y-step kernel);
+//            the slab receives v = G on the mask and Z elsewhere
+//   phase B  W-step of every row (i1, :, i3) (step 4, Eq. (subquKKT))
+//   phase C  forward mode-3 DFT of every tube of W (step 7, Eq. (bar BA-k));
+//            the residual spectrum R~ = W~ - Z~ is stored
 #pragma once
 
 namespace tc {
@@ -15,26 +16,34 @@ enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2 };
 
 constexpr int kSlabMaxThreads = 288;
 
+// Threads per CTA of the register-FFT variants: long tubes need the 255-register
+// budget of two warps per scheduler (nine warps put three on one scheduler and
+// cap a thread at 168 registers); tubes beyond the thread count loop.
+__host__ __device__ constexpr int slab_max_threads(int L) { return (L >= 64) ? 256 : kSlabMaxThreads; }
+
+// Odd stride between tubes in the slab (n3 values per tube).
+__host__ __device__ inline int slab_stride(int n3) { return n3 | 1; }
+
 struct SlabLayout {
-  size_t xrow, wtab, red, spec, spat, total;  // byte offsets and total shared bytes
-  size_t slab_bytes;                          // bytes of the slab buffers per CTA
+  size_t wtab, red, msk, stw, spec, spat, total;  // byte offsets and total shared bytes
+  size_t slab_bytes;                         // bytes of the slab buffers per CTA
 };
 
-// Shared-memory layout.  With a register FFT (specialised) only the spatial
-// slab n3 x n2 is kept; the generic transform also stages the half spectrum.
 template <typename T>
-__host__ __device__ inline SlabLayout slab_layout(int n2, int n3, int r, bool specialised, bool slabs_in_smem) {
+__host__ __device__ inline SlabLayout slab_layout(int n2, int n3, bool specialised, bool slabs_in_smem) {
   SlabLayout L{};
   const int S = n3 / 2 + 1;
   size_t off = 0;
-  L.xrow = off;
-  off = align_up(off + sizeof(cx<T>) * S * r, 16);
   L.wtab = off;
-  off = align_up(off + sizeof(T) * 4 * n2, 16);
+  off = align_up(off + sizeof(T) * 6 * n2, 16);
   L.red = off;
   off = align_up(off + sizeof(double) * 4 * 32, 16);
+  L.msk = off;  // row-major mask bits: [n3][ceil(n2/32)]
+  off = align_up(off + sizeof(uint32_t) * (size_t)n3 * ((n2 + 31) / 32), 16);
+  L.stw = off;  // per row and mask word: start of the run of missing entries entering the word
+  off = align_up(off + sizeof(int) * (size_t)n3 * ((n2 + 31) / 32), 16);
   const size_t spec_bytes = specialised ? 0 : align_up(sizeof(cx<T>) * (size_t)S * n2, 16);
-  const size_t spat_bytes = align_up(sizeof(T) * (size_t)n3 * n2, 16);
+  const size_t spat_bytes = align_up(sizeof(T) * (size_t)n2 * slab_stride(n3), 16);
   L.slab_bytes = spec_bytes + spat_bytes;
   if (slabs_in_smem) {
     L.spec = off;
@@ -49,113 +58,133 @@ __host__ __device__ inline SlabLayout slab_layout(int n2, int n3, int r, bool sp
 }
 
 // ---------------------------------------------------------------------------
-// W-step of one spatial row (i1, :, i3) in residual form.
+// W-step of one row (i1, :, i3) (Eq. (subquKKT), Eq. (Wkiom)).
 //
-// Eq. (subquKKT): for a missing (i, j), (W K_{mu rho2})_ij = Z_ij with
-// K_{mu rho2} = (1+mu) I + rho2 K^T K (tridiagonal); W_ij = G_ij on the mask.
-// With W = Z + R the unknown R solves the same tridiagonal system with
-// right-hand side -(mu + rho2 deg_j) z_j + rho2 (z_{j-1} + z_{j+1}) at missing
-// entries and g_j - z_j at observed ones (identity rows).  Observed entries
-// split the row into runs; the LU pivots of a run depend only on the position
-// in the run and on whether it starts at j = 0, so their inverses come from a
-// table and each sweep is a single fused multiply-add chain:
-//   forward   d_j = a_j d_{j-1} + b_j,   backward  r_j = c_j r_{j+1} + d_j.
-// The last entry of the row (one neighbour) gets its pivot computed here.
-// On return row[j] holds r_j = w_j - z_j.
+// For a missing j, (W K_{mu rho2})_j = Z_j with K_{mu rho2} = (1+mu) I +
+// rho2 K^T K (tridiagonal); W_j = G_j on the mask (identity rows).  On entry
+// the row holds v_j = G_j on the mask and Z_j elsewhere; the observed
+// neighbours of a missing entry enter through the elimination itself.  The
+// LU pivots of a run of missing entries depend only on the position p in the
+// run, on whether the run starts at j = 0 and on whether j is the last entry
+// of the row (the first and last entries have one neighbour), so their
+// inverses come from a table and each sweep is a single fused multiply-add
+// chain:
+//   forward   d_j = a_j d_{j-1} + b_j,   a_j = rho2 inv_j,  b_j = v_j inv_j
+//   backward  w_j = c_j w_{j+1} + d_j,   c_j = rho2 inv_j (0 at j = n2-1)
+// with a_j = c_j = 0, b_j = v_j at observed entries.  On return the row
+// holds W.  row[j] is at col[j * LP].  The row is processed 16 entries at a
+// time (half a mask word): the entries are read into registers first, so
+// only the multiply-add chain stays on the critical path.  The run start entering
+// each word is saved by the forward sweep for the backward one.
+//
+// wtab: [6][n2] inv1, inv0 (runs starting at j = 0 / j > 0), c1 = rho2 inv1,
+//       c0 = rho2 inv0, e1, e0 (inverse pivot when the run ends at j = n2-1)
+// rowm: the row's mask bits along j (word j / 32, bit j % 32)
+// rowst: per-word run starts (written here)
 // ---------------------------------------------------------------------------
+// Fills the [6][n2] W-step table of wstep_sweeps in FP64, rounded to T.
+// Pivots of a run of missing entries by position p: the first has diagonal
+// 1 + mu + rho2 (run at j = 0, one neighbour) or 1 + mu + 2 rho2; each later
+// one subtracts rho2^2 times the previous inverse pivot; at j = n2 - 1 the
+// diagonal loses one rho2 (one neighbour).
 template <typename T>
-__device__ void wstep_row(T* __restrict__ row, const T* __restrict__ g, const uint32_t* __restrict__ m, int n2,
-                          int words, T mu, T rho2, const T* __restrict__ wtab) {
-  const T* inv1 = wtab;           // runs starting at j = 0
-  const T* inv0 = wtab + n2;      // runs starting at j > 0
-  const T* c1 = wtab + 2 * n2;    // rho2 * inv1
-  const T* c0 = wtab + 3 * n2;    // rho2 * inv0
-  const T rho2sq = rho2 * rho2;
-  // ---- forward sweep -------------------------------------------------------
-  T dprev = T(0), zprev = T(0);
-  T z = row[0];
-  int p = -1;
-  bool st0 = false;
-  T invprev = T(0);
-  for (int w = 0; w < words; ++w) {
-    const uint32_t mw = __ldg(m + w);
-    T gv[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int j = 32 * w + q;
-      gv[q] = (j < n2) ? __ldg(g + j) : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const int j = 32 * w + q;
-      if (j < n2) {
-        const T znext = (j + 1 < n2) ? row[j + 1] : T(0);
-        T a, b;
-        if ((mw >> q) & 1u) {
-          a = T(0);
-          b = gv[q] - z;
-          p = -1;
-        } else {
-          if (p < 0) st0 = (j == 0);
-          ++p;
-          T inv;
-          if (j == n2 - 1 && n2 > 1) {
-            inv = T(1) / (T(1) + mu + rho2 - ((p > 0) ? rho2sq * invprev : T(0)));
-          } else {
-            inv = st0 ? inv1[p] : inv0[p];
-          }
-          invprev = inv;
-          const T deg = T((j > 0) + (j + 1 < n2));
-          const T e = -(mu + rho2 * deg) * z + rho2 * (zprev + znext);
-          a = rho2 * inv;
-          b = e * inv;
-        }
-        const T d = fma(a, dprev, b);
-        row[j] = d;
-        dprev = d;
-        zprev = z;
-        z = znext;
-      }
+__host__ __device__ inline void wstep_tables(T* w, int n2, double mu, double rho2) {
+  const double first[2] = {1.0 + mu + rho2 * (n2 > 1 ? 1.0 : 0.0), 1.0 + mu + 2.0 * rho2};
+  const double last[2] = {first[0], 1.0 + mu + rho2};
+  for (int b = 0; b < 2; ++b) {  // b = 0: run starting at j = 0; b = 1: j > 0
+    double prev = 0.0;
+    for (int q = 0; q < n2; ++q) {
+      const double sub = (q > 0) ? rho2 * rho2 * prev : 0.0;
+      const double inv = 1.0 / (((q > 0) ? 1.0 + mu + 2.0 * rho2 : first[b]) - sub);
+      const double inv_last = 1.0 / (last[b] - sub);
+      w[(size_t)b * n2 + q] = (T)inv;
+      w[(size_t)(2 + b) * n2 + q] = (T)(rho2 * inv);
+      w[(size_t)(4 + b) * n2 + q] = (T)inv_last;
+      prev = inv;
     }
   }
-  // ---- backward sweep ------------------------------------------------------
-  T rnext = T(0);
-  int pb = -1, rs = 0;
-  for (int w = words - 1; w >= 0; --w) {
-    const uint32_t mw = __ldg(m + w);
+}
+
+template <typename T>
+__device__ void wstep_sweeps(T* __restrict__ col, int LP, const uint32_t* __restrict__ rowm, int* __restrict__ rowst,
+                             int n2, T rho2, const T* __restrict__ wtab) {
+  constexpr int CH = 16;  // entries held in registers at a time (half a mask word)
+  const int words = (n2 + 31) >> 5;
+  // ---- forward: d_j = a_j d_{j-1} + b_j --------------------------------------
+  T d = T(0);
+  int st = 0;  // start index of the current run of missing entries
+  for (int w = 0; w < words; ++w) {
+    const uint32_t mw = rowm[w];
+    rowst[w] = st;
 #pragma unroll
-    for (int q = 31; q >= 0; --q) {
-      const int j = 32 * w + q;
-      if (j < n2) {
-        const T d = row[j];
-        T c = T(0);
-        if (!((mw >> q) & 1u)) {
-          if (pb < 0) {  // right end of a run: locate its start
-            const uint32_t below = q ? (mw & ((1u << q) - 1u)) : 0u;
-            const int po = below ? (32 * w + 31 - __clz(below)) : prev_observed(m, 32 * w);
-            rs = po + 1;
-            pb = j - rs;
+    for (int h = 0; h < 32 / CH; ++h) {
+      const int base = 32 * w + CH * h;
+      const int qn = min(CH, n2 - base);
+      T v[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < qn) v[q] = col[(base + q) * LP];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        if (q < qn) {
+          const int j = base + q;
+          if ((mw >> (CH * h + q)) & 1u) {
+            d = v[q];
+            st = j + 1;
+          } else {
+            const T inv = wtab[((st == 0) ? 0 : n2) + ((j == n2 - 1) ? 4 * n2 : 0) + (j - st)];
+            d = fma(rho2 * inv, d, v[q] * inv);
+            v[q] = d;
           }
-          if (j < n2 - 1) c = (rs == 0) ? c1[pb] : c0[pb];
-          --pb;
-        } else {
-          pb = -1;
         }
-        const T rv = fma(c, rnext, d);
-        row[j] = rv;
-        rnext = rv;
       }
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < qn) col[(base + q) * LP] = v[q];
+    }
+  }
+  // ---- backward: w_j = c_j w_{j+1} + d_j (observed slots already hold G) -----
+  T wn = T(0);
+  for (int w = words - 1; w >= 0; --w) {
+    const uint32_t mw = rowm[w];
+    const int stw = rowst[w];
+#pragma unroll
+    for (int h = 32 / CH - 1; h >= 0; --h) {
+      const int base = 32 * w + CH * h;
+      const int qn = min(CH, n2 - base);  // may be <= 0 in the last word
+      T v[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < qn) v[q] = col[(base + q) * LP];
+#pragma unroll
+      for (int q = CH - 1; q >= 0; --q) {
+        if (q < qn) {
+          const int j = base + q;
+          const int b = CH * h + q;  // bit of j in the word
+          if ((mw >> b) & 1u) {
+            wn = v[q];
+          } else {
+            const uint32_t below = mw & ((1u << b) - 1u);
+            const int rs = below ? 32 * w + 32 - __clz(below) : stw;  // start of the run holding j
+            const T c = (j < n2 - 1) ? wtab[((rs == 0) ? 2 * n2 : 3 * n2) + (j - rs)] : T(0);
+            wn = fma(c, wn, v[q]);
+            v[q] = wn;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < qn) col[(base + q) * LP] = v[q];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Generic (any n3) direct transforms of one tube, used when no register FFT
-// is specialised for n3: the sums of Eq. (bar BA-k) and Eq. (barAAk).
+// Generic (any n3) direct transforms of one tube: the sums of Eq. (bar BA-k)
+// and Eq. (barAAk).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int pstride, int n3,
-                              const cx<T>* __restrict__ twg) {
+__device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int n3, const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
   const bool even = (n3 % 2) == 0;
   const int kmax = even ? S - 2 : S - 1;  // slices with a conjugate partner
@@ -168,128 +197,186 @@ __device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int pstri
       acc += T(2) * (v.re * w.re + v.im * w.im);  // 2 Re(v conj(w))
     }
     if (even) acc += ((l & 1) ? -spec[(S - 1) * sstride].re : spec[(S - 1) * sstride].re);
-    spat[l * pstride] = acc * inv;
+    spat[l] = acc * inv;
   }
 }
 
+// Forward transform of a tube minus the spectrum zsub (R~ = W~ - Z~).
 template <typename T>
-__device__ void generic_rdft(const T* spat, int pstride, cx<T>* out, size_t ostride, int n3,
-                             const cx<T>* __restrict__ twg) {
+__device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, cx<T>* out, size_t stride, int n3,
+                                 const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
   for (int k = 0; k < S; ++k) {
     cx<T> acc = {T(0), T(0)};
     for (int l = 0; l < n3; ++l) {
       const cx<T> w = twg[(int)(((long long)k * l) % n3)];
-      const T x = spat[l * pstride];
+      const T x = spat[l];
       acc.re += x * w.re;
       acc.im += x * w.im;
     }
     if (k == 0 || (2 * k == n3)) acc.im = T(0);
-    out[k * ostride] = acc;
+    out[k * stride] = acc - zsub[k * stride];
   }
 }
 
 // ---------------------------------------------------------------------------
 // MODE_ITER: phases A, B, C (init != 0: W = P_Omega(G), the initial point, in
 //            place of the W-step).
-// MODE_W   : W = iDFT(X~Y~ + R~); optional copy to Wout (column-major), partial
+// MODE_W   : W = iDFT(Z~ + R~); optional copy to Wout (column-major), partial
 //            sums ||W||^2 and ||K unfold(W,2)||^2.
 // MODE_R   : R = iDFT(R~); partial sums ||R||^2 and ||P_Omega R||^2.
+// Layouts used here: G row-major [i1][n3][n2] and mask words tube-major
+// [i1][n2][ceil(n3/32)] (written by k_pack).
 // ---------------------------------------------------------------------------
 template <typename T, int L, int MODE>
-__global__ void __launch_bounds__(kSlabMaxThreads, 1)
+__global__ void __launch_bounds__(slab_max_threads(L), 1)
     k_slab(Dev<T> d, T* __restrict__ Wout, int slabs_in_smem, int init) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int i1 = blockIdx.x;
-  const int n1 = d.n1, n2 = d.n2, r = d.r;
+  const int n1 = d.n1, n2 = d.n2;
   const int n3 = (L > 0) ? L : d.n3;
   const int S = n3 / 2 + 1;
+  const int LP = slab_stride(n3);
+  const int lw = d.words;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (L > 0 && (d.n3 != L || n2 > nt)) {
+  if (L > 0 && d.n3 != L) {
     if (tid == 0) set_err(d.err, DEV_BAD_LAUNCH);
     return;
   }
-  const SlabLayout lay = slab_layout<T>(n2, n3, r, L > 0, slabs_in_smem != 0);
-  cx<T>* xrow = reinterpret_cast<cx<T>*>(smem + lay.xrow);
+  const SlabLayout lay = slab_layout<T>(n2, n3, L > 0, slabs_in_smem != 0);
   T* wtab = reinterpret_cast<T*>(smem + lay.wtab);
   double* red = reinterpret_cast<double*>(smem + lay.red);
+  uint32_t* msk = reinterpret_cast<uint32_t*>(smem + lay.msk);
+  int* stw = reinterpret_cast<int*>(smem + lay.stw);
   unsigned char* slab_base =
       slabs_in_smem ? smem : reinterpret_cast<unsigned char*>(d.scratch) + (size_t)i1 * lay.slab_bytes;
   cx<T>* spec = reinterpret_cast<cx<T>*>(slab_base + lay.spec);
   T* spat = reinterpret_cast<T*>(slab_base + lay.spat);
+  const cx<T>* zrow = d.Zt + (size_t)i1 * S * n2;
+  const cx<T>* rrow = d.Rt + (size_t)i1 * S * n2;
+  const T* Gi = d.G + (size_t)i1 * n2 * n3;
+  const uint32_t* Mi = d.mask + (size_t)i1 * n2 * lw;
+  const bool wsolve = (MODE == MODE_ITER) && !init && d.rho2 != T(0);
+  const T zfac = init ? T(0) : ((d.rho2 == T(0)) ? T(1) / (T(1) + d.mu) : T(1));
 
-  const bool synth = (MODE != MODE_R);
-  if (synth) {
-    for (int idx = tid; idx < S * r; idx += nt) {
-      const int k = idx / r, s = idx - k * r;
-      xrow[idx] = d.Xt[(size_t)(k * r + s) * n1 + i1];
+  const int mwords = (n2 + 31) >> 5;
+  if (wsolve) {
+    for (int j = tid; j < 6 * n2; j += nt) wtab[j] = d.winv[j];
+    if (L == 0) {
+      for (int j = tid; j < n3 * mwords; j += nt) msk[j] = 0u;
+      __syncthreads();
     }
   }
-  if (MODE == MODE_ITER) {
-    for (int j = tid; j < 4 * n2; j += nt) wtab[j] = d.winv[j];
-  }
-  __syncthreads();
 
-  // ---- phase A: spectrum of each tube, inverse transform ---------------------
+  // ---- phase A: inverse transform of each tube; v = G on the mask ------------
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
-    const int t = tid;
-    if (t < n2) {
-      cx<T> X[SL];
-#pragma unroll
-      for (int k = 0; k < SL; ++k) {
-        X[k] = (MODE == MODE_ITER) ? cx<T>{T(0), T(0)} : d.Rt[((size_t)i1 * SL + k) * n2 + t];
-      }
-      if (synth) {
-        // s-chunks outside, slices inside: all loads of a chunk are independent
-        for (int s0 = 0; s0 < r; s0 += 4) {
-#pragma unroll
-          for (int k = 0; k < SL; ++k) {
-            const cx<T>* yk = d.Yt + ((size_t)k * r + s0) * n2 + t;
-            const cx<T>* xk = xrow + k * r + s0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (s0 + q < r) cfma(X[k], xk[q], ldg_cx(yk + (size_t)q * n2));
+    constexpr int LW = (L + 31) / 32;
+    if (MODE == MODE_ITER) {
+      // G (row-major, read coalesced) is staged into the slab, transposed to the
+      // tube-major layout, with asynchronous copies issued ahead of the transforms;
+      // each tube then picks its observed values from its own column.
+      int l = tid / n2, t = tid - (tid / n2) * n2;
+      if (slabs_in_smem) {
+        for (int e = tid; e < n3 * n2; e += nt) {
+          cp_async_elem(spat + t * LP + l, Gi + e);
+          t += nt;
+          while (t >= n2) {
+            t -= n2;
+            ++l;
+          }
+        }
+        cp_async_wait_all();
+      } else {
+        for (int e = tid; e < n3 * n2; e += nt) {
+          spat[(size_t)t * LP + l] = __ldg(Gi + e);
+          t += nt;
+          while (t >= n2) {
+            t -= n2;
+            ++l;
           }
         }
       }
+      __syncthreads();
+    }
+    for (int t0 = 0; t0 < n2; t0 += nt) {
+      const int t = t0 + tid;
+      if (t0 + (tid & ~31) >= n2) continue;  // whole warp past the last column (warp-uniform)
+      const bool act = t < n2;
+      cx<T> X[SL];
+#pragma unroll
+      for (int k = 0; k < SL; ++k) {
+        const size_t o = (size_t)k * n2 + (act ? t : 0);
+        if (MODE == MODE_ITER) X[k] = ldg_cx(zrow + o);
+        else if (MODE == MODE_W) X[k] = ldg_cx(zrow + o) + ldg_cx(rrow + o);
+        else X[k] = ldg_cx(rrow + o);
+      }
       T x[L];
       fft::irfft<T, L>(X, x);
+      if (MODE == MODE_ITER) {
+        uint32_t mw[LW];
 #pragma unroll
-      for (int l = 0; l < L; ++l) spat[l * n2 + t] = x[l];
+        for (int w = 0; w < LW; ++w) mw[w] = act ? __ldg(Mi + (size_t)t * LW + w) : 0u;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          const bool ob = (mw[l >> 5] >> (l & 31)) & 1u;
+          if (wsolve) {
+            const uint32_t row_bits = __ballot_sync(0xffffffffu, ob);
+            if ((tid & 31) == 0) msk[l * mwords + (t >> 5)] = row_bits;
+          }
+          x[l] = ob ? spat[(size_t)(act ? t : 0) * LP + l] : x[l] * zfac;
+        }
+      }
+      if (act) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) spat[t * LP + l] = x[l];
+      }
     }
   } else {
     for (int t = tid; t < n2; t += nt) {
       for (int k = 0; k < S; ++k) {
-        cx<T> acc = (MODE == MODE_ITER) ? cx<T>{T(0), T(0)} : d.Rt[((size_t)i1 * S + k) * n2 + t];
-        if (synth) {
-          const cx<T>* yk = d.Yt + (size_t)k * r * n2 + t;
-          const cx<T>* xk = xrow + k * r;
-          for (int s = 0; s < r; ++s) cfma(acc, xk[s], yk[(size_t)s * n2]);
-        }
-        spec[k * n2 + t] = acc;
+        const size_t o = (size_t)k * n2 + t;
+        cx<T> v;
+        if (MODE == MODE_ITER) v = zrow[o];
+        else if (MODE == MODE_W) v = zrow[o] + rrow[o];
+        else v = rrow[o];
+        spec[k * n2 + t] = v;
       }
     }
     __syncthreads();
-    for (int t = tid; t < n2; t += nt) generic_irdft<T>(spec + t, n2, spat + t, n2, n3, d.twg);
+    for (int t = tid; t < n2; t += nt) {
+      T* col = spat + (size_t)t * LP;
+      generic_irdft<T>(spec + t, n2, col, n3, d.twg);
+      if (MODE == MODE_ITER) {
+        for (int w = 0; w < lw; ++w) {
+          const uint32_t mw = __ldg(Mi + (size_t)t * lw + w);
+          for (int q = 0; q < 32 && 32 * w + q < n3; ++q) {
+            const int l = 32 * w + q;
+            const bool ob = (mw >> q) & 1u;
+            if (wsolve && ob) atomicOr(msk + l * mwords + (t >> 5), 1u << (t & 31));
+            col[l] = ob ? __ldg(Gi + (size_t)l * n2 + t) : col[l] * zfac;
+          }
+        }
+      }
+    }
   }
   __syncthreads();
 
   // ---- phase B: rows ------------------------------------------------------
   if (MODE == MODE_W || MODE == MODE_R) {
     double a = 0.0, b = 0.0;
-    for (int e = tid; e < n3 * n2; e += nt) {
-      const int l = e / n2, j = e - l * n2;
-      const T v = spat[e];
+    for (int e = tid; e < n2 * n3; e += nt) {
+      const int j = e / n3, l = e - j * n3;
+      const T v = spat[j * LP + l];
       a += (double)v * (double)v;
       if (MODE == MODE_W) {
         if (j + 1 < n2) {
-          const double dv = (double)v - (double)spat[e + 1];
+          const double dv = (double)v - (double)spat[(j + 1) * LP + l];
           b += dv * dv;
         }
         if (Wout) Wout[(size_t)i1 + (size_t)n1 * ((size_t)j + (size_t)n2 * l)] = v;
       } else {
-        if (bit_at(d.mask + ((size_t)i1 * n3 + l) * d.words, j)) b += (double)v * (double)v;
+        if ((__ldg(Mi + (size_t)j * lw + (l >> 5)) >> (l & 31)) & 1u) b += (double)v * (double)v;
       }
     }
     block_sum2(a, b, red);
@@ -300,43 +387,29 @@ __global__ void __launch_bounds__(kSlabMaxThreads, 1)
     }
     return;
   }
-
-  if (init || d.rho2 == T(0)) {
-    // W = P_Omega(G) (initial point) or the entry-wise form of Eq. (Wkiom)
-    // with rho2 = 0: W = Z / (1 + mu) off the mask.
-    const T shrink = init ? T(-1) : -d.mu / (T(1) + d.mu);
-    for (int e = tid; e < n3 * n2; e += nt) {
-      const int l = e / n2, j = e - l * n2;
-      const size_t rowi = (size_t)i1 * n3 + l;
-      const T z = spat[e];
-      spat[e] = bit_at(d.mask + rowi * d.words, j) ? __ldg(d.G + rowi * n2 + j) - z : shrink * z;
-    }
-  } else {
-    for (int l = tid; l < n3; l += nt) {
-      const size_t rowi = (size_t)i1 * n3 + l;
-      wstep_row<T>(spat + (size_t)l * n2, d.G + rowi * n2, d.mask + rowi * d.words, n2, d.words, d.mu, d.rho2,
-                   wtab);
-    }
+  if (wsolve) {
+    for (int l = tid; l < n3; l += nt)
+      wstep_sweeps<T>(spat + l, LP, msk + l * mwords, stw + l * mwords, n2, d.rho2, wtab);
+    __syncthreads();
   }
-  __syncthreads();
 
-  // ---- phase C: forward transform, store R~ --------------------------------
+  // ---- phase C: forward transform, R~ = W~ - Z~ ------------------------------
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
-    const int t = tid;
-    if (t < n2) {
+    for (int t = tid; t < n2; t += nt) {
       T x[L];
 #pragma unroll
-      for (int l = 0; l < L; ++l) x[l] = spat[l * n2 + t];
+      for (int l = 0; l < L; ++l) x[l] = spat[t * LP + l];
       cx<T> X[SL];
       fft::rfft<T, L>(x, X);
       cx<T>* rt = d.Rt + (size_t)i1 * SL * n2 + t;
+      const cx<T>* zt = zrow + t;
 #pragma unroll
-      for (int k = 0; k < SL; ++k) rt[(size_t)k * n2] = X[k];
+      for (int k = 0; k < SL; ++k) rt[(size_t)k * n2] = X[k] - ldg_cx(zt + (size_t)k * n2);
     }
   } else {
     for (int t = tid; t < n2; t += nt) {
-      generic_rdft<T>(spat + t, n2, d.Rt + (size_t)i1 * S * n2 + t, (size_t)n2, n3, d.twg);
+      generic_rdft_sub<T>(spat + (size_t)t * LP, zrow + t, d.Rt + (size_t)i1 * S * n2 + t, (size_t)n2, n3, d.twg);
     }
   }
 }

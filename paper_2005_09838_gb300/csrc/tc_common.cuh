@@ -93,76 +93,18 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 constexpr int kMaxRank = 32;
 
-// ---------------------------------------------------------------------------
-// Double-float arithmetic: an unevaluated sum hi + lo of two floats carries
-// about 48 significant bits at FP32 instruction rates (GB300's FP64 rate is a
-// small fraction of its FP32 rate).  Error-free transformations: TwoSum
-// (Knuth), TwoProduct through the fused multiply-add.  The _rn intrinsics keep
-// the compiler from contracting or reassociating these sequences.
-// ---------------------------------------------------------------------------
-struct dfl {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element size");
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
 }
 
-__device__ __forceinline__ dfl df_norm(float s, float e) {
-  const float hi = __fadd_rn(s, e);
-  return dfl{hi, __fsub_rn(e, __fsub_rn(hi, s))};
-}
-
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  float s, e;
-  two_sum(a.hi, b.hi, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-  return df_norm(s, e);
-}
-
-// acc += x * y with the product formed exactly
-__device__ __forceinline__ void df_fma(dfl& acc, float x, float y) {
-  const float p = __fmul_rn(x, y);
-  const float pe = __fmaf_rn(x, y, -p);
-  float s, e;
-  two_sum(acc.hi, p, s, e);
-  e = __fadd_rn(e, __fadd_rn(acc.lo, pe));
-  acc = df_norm(s, e);
-}
-
-// acc += a * y with a double-float a
-__device__ __forceinline__ void df_fma(dfl& acc, dfl a, float y) {
-  const float p = __fmul_rn(a.hi, y);
-  float pe = __fmaf_rn(a.hi, y, -p);
-  pe = __fmaf_rn(a.lo, y, pe);
-  float s, e;
-  two_sum(acc.hi, p, s, e);
-  e = __fadd_rn(e, __fadd_rn(acc.lo, pe));
-  acc = df_norm(s, e);
-}
-
-__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
-  return dfl{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-}
-
-__device__ __forceinline__ dfl df_warp_sum(dfl v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-  return v;
-}
-
-__device__ __forceinline__ dfl df_from_double(double x) {
-  const float hi = (float)x;
-  return dfl{hi, (float)(x - (double)hi)};
-}
-
-__device__ __forceinline__ double df_to_double(dfl v) { return (double)v.hi + (double)v.lo; }
-
-// Complex double-float accumulator.
-struct cdfl {
-  dfl re, im;
-};
+// Wait for every cp.async of this thread (the block still needs a barrier).
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 }  // namespace tc

@@ -5,9 +5,11 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "tc_engine.h"
@@ -97,7 +99,7 @@ class Engine final : public EngineBase {
     n3_ = (int)p.n3;
     r_ = p.r;
     S_ = n3_ / 2 + 1;
-    words_ = (n2_ + 31) / 32;
+    words_ = (n3_ + 31) / 32;  // mask words per tube
     rp_ = pad_rank<T>(r_);
     const size_t N = (size_t)n1_ * n2_ * n3_;
     TC_CUDA_TRY(cudaGetDevice(&device_));
@@ -109,16 +111,18 @@ class Engine final : public EngineBase {
     // ---- state buffers -----------------------------------------------------------
     const size_t nx = (size_t)S_ * r_ * n1_, ny = (size_t)S_ * r_ * n2_, nrr = (size_t)S_ * r_ * r_;
     T* Gint = alloc<T>(N, err);
-    uint32_t* maskbits = alloc<uint32_t>((size_t)n1_ * n3_ * words_, err);
+    uint32_t* maskbits = alloc<uint32_t>((size_t)n1_ * n2_ * words_, err);
     cx<T>* Rt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
+    cx<T>* Zt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
+    const int ytiles = (n2_ + 31) / 32;
+    cx<double>* Ag = alloc<cx<double>>((size_t)S_ * ytiles * (r_ * (r_ + 1) / 2), err);
     cx<T>* Xt = alloc<cx<T>>(nx, err);
     Q_ = alloc<cx<T>>(nx, err);
     cx<T>* Tb = alloc<cx<T>>(nx, err);
     cx<T>* Yt = alloc<cx<T>>(ny, err);
-    cx<T>* Mm = alloc<cx<T>>(nrr, err);
+    cx<T>* Dg = alloc<cx<T>>(nrr, err);
     cx<T>* Gp = alloc<cx<T>>(nrr, err);
-    cx<T>* Gplo = alloc<cx<T>>(nrr, err);
-    T* winv = alloc<T>((size_t)4 * n2_, err);
+    T* winv = alloc<T>((size_t)6 * n2_, err);
     T* hinv = alloc<T>((size_t)2 * n1_, err);
     cx<T>* twg = alloc<cx<T>>((size_t)n3_, err);
     double* part = alloc<double>((size_t)n1_ * 4, err);
@@ -127,13 +131,14 @@ class Engine final : public EngineBase {
     if (!err.empty()) return TC_ERR_NOMEM;
 
     // ---- kernel variants and shared memory -------------------------------------------
-    specialised_ = pick_slab<T>(n3_, slab_) && ((n2_ + 31) / 32 * 32 <= kSlabMaxThreads);
+    specialised_ = pick_slab<T>(n3_, slab_);
     if (!specialised_) slab_table<T, 0>(slab_);
-    slab_threads_ = specialised_ ? (n2_ + 31) / 32 * 32 : 256;
-    SlabLayout lay = slab_layout<T>(n2_, n3_, r_, specialised_, true);
+    slab_threads_ = specialised_ ? std::min((n2_ + 31) / 32 * 32, slab_max_threads(n3_)) : 256;
+    slab_threads_ = std::max(slab_threads_, std::min(256, (n3_ + 31) / 32 * 32));  // one thread per W-step row
+    SlabLayout lay = slab_layout<T>(n2_, n3_, specialised_, true);
     slabs_in_smem_ = lay.total <= (size_t)optin;
     if (!slabs_in_smem_) {
-      lay = slab_layout<T>(n2_, n3_, r_, specialised_, false);
+      lay = slab_layout<T>(n2_, n3_, specialised_, false);
       T* scratch = alloc<T>(lay.slab_bytes / sizeof(T) * (size_t)n1_ + 16, err);
       if (!err.empty()) return TC_ERR_NOMEM;
       d_.scratch = scratch;
@@ -167,21 +172,9 @@ class Engine final : public EngineBase {
     // ---- host tables (FP64, rounded to T) ----------------------------------------------
     {
       const double mu = p.mu, rho1 = p.rho1, rho2 = p.rho2;
-      // W-step runs: inverse LU pivots by position in the run; runs starting at
-      // j = 0 have one neighbour at their first entry (when n2 > 1)
-      std::vector<T> w(4 * (size_t)n2_);
-      double inv = 1.0 / (1.0 + mu + rho2 * (n2_ > 1 ? 1.0 : 0.0));
-      for (int q = 0; q < n2_; ++q) {
-        if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
-        w[q] = (T)inv;
-        w[2 * n2_ + q] = (T)(rho2 * inv);
-      }
-      inv = 1.0 / (1.0 + mu + 2.0 * rho2);
-      for (int q = 0; q < n2_; ++q) {
-        if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
-        w[n2_ + q] = (T)inv;
-        w[3 * n2_ + q] = (T)(rho2 * inv);
-      }
+      // W-step runs: inverse LU pivots by position in the run
+      std::vector<T> w(6 * (size_t)n2_);
+      wstep_tables<T>(w.data(), n2_, mu, rho2);
       // H_rho1 = I + rho1 H^T H: diagonal 1 + rho1 deg_i, off-diagonal -rho1
       std::vector<T> h(2 * (size_t)n1_);
       double hi = 0.0;
@@ -215,11 +208,13 @@ class Engine final : public EngineBase {
     d_.G = Gint;
     d_.mask = maskbits;
     d_.Rt = Rt;
+    d_.Zt = Zt;
+    d_.Ag = Ag;
+    d_.ytiles = ytiles;
     d_.Xt = Xt;
     d_.Yt = Yt;
-    d_.Mm = Mm;
+    d_.Dg = Dg;
     d_.Gp = Gp;
-    d_.Gplo = Gplo;
     d_.Tb = Tb;
     d_.winv = winv;
     d_.hinv = hinv;
@@ -227,7 +222,7 @@ class Engine final : public EngineBase {
     d_.part = part;
     d_.part_k = part_k;
     d_.err = derr;
-    d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * 2.220446049250313e-16;
+    d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * (double)std::numeric_limits<T>::epsilon();
     TC_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), stream_));
 
     // ---- inputs --------------------------------------------------------------------------
@@ -255,7 +250,7 @@ class Engine final : public EngineBase {
         return TC_ERR_NOMEM;
       }
     }
-    k_pack<T><<<n1_ * n3_, 256, 0, stream_>>>(dG, dM, Gint, maskbits, n1_, n2_, n3_, words_);
+    k_pack<T><<<n1_ * n2_, 256, 0, stream_>>>(dG, dM, Gint, maskbits, n1_, n2_, n3_, words_);
     const int fgrid = 4 * 152;
     k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dY, Yt, n2_, r_, n3_, 1);
     if (dX) {
@@ -263,7 +258,9 @@ class Engine final : public EngineBase {
     } else {
       cudaMemsetAsync(Xt, 0, nx * sizeof(cx<T>), stream_);
     }
-    launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - X0*Y0)
+    k_synth_init<T><<<fgrid, 256, 0, stream_>>>(d_);                    // Z~0 = X~0 Y~0
+    k_gram_tiles<T><<<dim3(S_, ytiles), 256, 0, stream_>>>(d_);         // A of the first X-step
+    launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - Z0)
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(stream_);
     for (void* q : tmp) cudaFree(q);

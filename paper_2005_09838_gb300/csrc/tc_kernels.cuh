@@ -8,8 +8,9 @@
 //   W~Y~^H = X~A + R~Y~^H and X~'^H W~ = X~'^H X~ Y~ + X~'^H R~.
 //
 // Layouts (last index fastest):
-//   G    [n1][n3][n2]  real, observed values (0 off the mask)
-//   mask [n1][n3][words] bit j of word row (i1, i3) = entry (i1, j, i3) observed
+//   G    [n1][n3][n2]  real, observed values (0 off the mask), row-major
+//   mask [n1][n2][words] words = ceil(n3/32); bit i3 % 32 of word i3 / 32 of
+//                        tube (i1, i2) = entry (i1, i2, i3) observed
 //   Rt   [n1][S][n2]   complex
 //   Xt   [S][r][n1]    complex
 //   Yt   [S][r][n2]    complex
@@ -30,13 +31,15 @@ struct Dev {
   const T* G;
   const uint32_t* mask;
   cx<T>* Rt;
+  cx<T>* Zt;        // [n1][S][n2] Z~ = X~Y~ of the current factors (written by k_ystep)
   cx<T>* Xt;
   cx<T>* Yt;
-  cx<T>* Mm;        // [S][r][r] Y-step matrix I - G^+ G + G^+ E
-  cx<T>* Gp;        // [S][r][r] G^+ (high part)
-  cx<T>* Gplo;      // [S][r][r] G^+ - Gp (low part, FP32 path)
+  cx<double>* Ag;   // [S][ytiles][r(r+1)/2] partial Grams Y~Y~^H over 32-column tiles
+  int ytiles;       // ceil(n2 / 32)
+  cx<T>* Dg;        // [S][r][r] E - G of the Y-step (k_xstep)
+  cx<T>* Gp;        // [S][r][r] G^+
   cx<T>* Tb;        // [S][3][r][n1] X-step work arrays when shared memory is too small
-  const T* winv;    // [4][n2] W-step run tables: inverse pivots and rho2 * inverse pivots
+  const T* winv;    // [6][n2] W-step run tables (wstep_tables)
   const T* hinv;    // [2][n1] H_rho1 = I + rho1 H^T H: inverse pivots and rho1 * inverse pivots
   const cx<T>* twg; // [n3] exp(-2 pi i m / n3) for the generic transform
   T* scratch;       // per-CTA slabs when shared memory is too small
@@ -92,6 +95,6 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 
 }  // namespace tc
 
-#include "k_aux.cuh"
 #include "k_slab.cuh"
 #include "k_slice.cuh"
+#include "k_aux.cuh"

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <limits>
 #include <mutex>
 #include <string>
 
@@ -76,20 +77,7 @@ struct Carve {
 template <typename T>
 __global__ void k_static_tables(T* winv, T* hinv, cx<T>* twg, int n1, int n2, int n3, double mu, double rho1,
                                 double rho2) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double inv = 1.0 / (1.0 + mu + rho2 * (n2 > 1 ? 1.0 : 0.0));
-    for (int q = 0; q < n2; ++q) {
-      if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
-      winv[q] = (T)inv;
-      winv[2 * n2 + q] = (T)(rho2 * inv);
-    }
-    inv = 1.0 / (1.0 + mu + 2.0 * rho2);
-    for (int q = 0; q < n2; ++q) {
-      if (q > 0) inv = 1.0 / (1.0 + mu + 2.0 * rho2 - rho2 * rho2 * inv);
-      winv[n2 + q] = (T)inv;
-      winv[3 * n2 + q] = (T)(rho2 * inv);
-    }
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) wstep_tables<T>(winv, n2, mu, rho2);
   if (blockIdx.x == 1 && threadIdx.x == 0) {
     double hi = 0.0;
     for (int i = 0; i < n1; ++i) {
@@ -134,14 +122,14 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
-  const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, words = (n2 + 31) / 32;
+  const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, words = (n3 + 31) / 32;
   const int rp = pad_rank<T>(r);
   const size_t N = (size_t)n1 * n2 * n3;
   const size_t nx = (size_t)S * r * n1, ny = (size_t)S * r * n2, nrr = (size_t)S * r * r;
 
-  SlabLayout lay = slab_layout<T>(n2, n3, r, false, true);
+  SlabLayout lay = slab_layout<T>(n2, n3, false, true);
   const bool slabs_in_smem = lay.total <= (size_t)optin;
-  if (!slabs_in_smem) lay = slab_layout<T>(n2, n3, r, false, false);
+  if (!slabs_in_smem) lay = slab_layout<T>(n2, n3, false, false);
   XLayout xl = xstep_layout<T>(n1, n2, r, true);
   const bool xsmem = xl.total <= (size_t)optin;
   if (!xsmem) xl = xstep_layout<T>(n1, n2, r, false);
@@ -153,16 +141,18 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   Carve cv{base};
   Dev<T> d{};
   T* Gint = cv.take<T>(N);
-  uint32_t* maskbits = cv.take<uint32_t>((size_t)n1 * n3 * words);
+  uint32_t* maskbits = cv.take<uint32_t>((size_t)n1 * n2 * words);
   d.Rt = cv.take<cx<T>>((size_t)n1 * S * n2);
+  d.Zt = cv.take<cx<T>>((size_t)n1 * S * n2);
+  d.ytiles = (n2 + 31) / 32;
+  d.Ag = cv.take<cx<double>>((size_t)S * d.ytiles * (r * (r + 1) / 2));
   d.Xt = cv.take<cx<T>>(nx);
   cx<T>* Q = cv.take<cx<T>>(nx);
   d.Tb = cv.take<cx<T>>(nx);
   d.Yt = cv.take<cx<T>>(ny);
-  d.Mm = cv.take<cx<T>>(nrr);
+  d.Dg = cv.take<cx<T>>(nrr);
   d.Gp = cv.take<cx<T>>(nrr);
-  d.Gplo = cv.take<cx<T>>(nrr);
-  T* winv = cv.take<T>((size_t)4 * n2);
+  T* winv = cv.take<T>((size_t)6 * n2);
   T* hinv = cv.take<T>((size_t)2 * n1);
   cx<T>* twg = cv.take<cx<T>>((size_t)n3);
   d.part = cv.take<double>((size_t)n1 * 4);
@@ -188,7 +178,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   d.winv = winv;
   d.hinv = hinv;
   d.twg = twg;
-  d.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r * 2.220446049250313e-16;
+  d.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r * (double)std::numeric_limits<T>::epsilon();
 
   // ---- kernels (generic mode-3 transform) ------------------------------------------------
   SlabFn<T> slab[3];
@@ -205,13 +195,15 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   // the array keeps the previous call's contents: clear what must start at zero
   cudaMemsetAsync(d.err, 0, sizeof(int), st);
   k_static_tables<T><<<3, 256, 0, st>>>(winv, hinv, twg, n1, n2, n3, p.mu, p.rho1, p.rho2);
-  k_pack<T><<<n1 * n3, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, words);
+  k_pack<T><<<n1 * n2, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, words);
   k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(Y0), d.Yt, n2, r, n3, 1);
   if (X0) {
     k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(X0), d.Xt, n1, r, n3, 0);
   } else {
     cudaMemsetAsync(d.Xt, 0, nx * sizeof(cx<T>), st);
   }
+  k_synth_init<T><<<fgrid, 256, 0, st>>>(d);
+  k_gram_tiles<T><<<dim3(S, d.ytiles), 256, 0, st>>>(d);
   slab[MODE_ITER]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 1);
   for (int it = 0; it < n_iters; ++it) {
     qcon<<<dim3(S, (n1 + 31) / 32), kSliceThreads, qsm, st>>>(d, Q);
