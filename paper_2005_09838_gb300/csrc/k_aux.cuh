@@ -6,24 +6,23 @@ namespace tc {
 
 
 // G (column-major, i1 fastest) and the byte mask -> the internal layouts:
-// G row-major [i1][i3][i2] (coalesced for tube-per-thread loads) and mask
-// words tube-major [i1][i2][ceil(n3/32)] (bit i3 % 32 of word i3 / 32).  One
-// CTA per tube (i1, i2).
+// G row-major [i1][i3][i2] and mask words row-major [i1][i3][ceil(n2/32)]
+// (bit i2 % 32 of word i2 / 32).  One CTA per row (i1, :, i3).
 template <typename T>
 __global__ void k_pack(const T* __restrict__ Gin, const uint8_t* __restrict__ Min, T* __restrict__ Gout,
-                       uint32_t* __restrict__ Mout, int n1, int n2, int n3, int words) {
-  const int tube = blockIdx.x;  // i1 * n2 + i2
-  const int i1 = tube / n2, i2 = tube - i1 * n2;
-  for (int l0 = 0; l0 < words * 32; l0 += blockDim.x) {
-    const int l = l0 + threadIdx.x;
+                       uint32_t* __restrict__ Mout, int n1, int n2, int n3, int mw) {
+  const int row = blockIdx.x;  // i1 * n3 + i3
+  const int i1 = row / n3, l = row - i1 * n3;
+  for (int t0 = 0; t0 < mw * 32; t0 += blockDim.x) {
+    const int t = t0 + threadIdx.x;
     bool obs = false;
-    if (l < n3) {
-      const size_t src = (size_t)i1 + (size_t)n1 * ((size_t)i2 + (size_t)n2 * l);
+    if (t < n2) {
+      const size_t src = (size_t)i1 + (size_t)n1 * ((size_t)t + (size_t)n2 * l);
       obs = Min[src] != 0;
-      Gout[((size_t)i1 * n3 + l) * n2 + i2] = obs ? Gin[src] : T(0);
+      Gout[(size_t)row * n2 + t] = obs ? Gin[src] : T(0);
     }
     const unsigned bits = __ballot_sync(0xffffffffu, obs);
-    if ((threadIdx.x & 31) == 0 && l < words * 32) Mout[(size_t)tube * words + (l >> 5)] = bits;
+    if ((threadIdx.x & 31) == 0 && t < mw * 32) Mout[(size_t)row * mw + (t >> 5)] = bits;
   }
 }
 

@@ -14,12 +14,11 @@ namespace tc {
 
 enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2 };
 
-constexpr int kSlabMaxThreads = 288;
-
-// Threads per CTA of the register-FFT variants: long tubes need the 255-register
-// budget of two warps per scheduler (nine warps put three on one scheduler and
-// cap a thread at 168 registers); tubes beyond the thread count loop.
-__host__ __device__ constexpr int slab_max_threads(int L) { return (L >= 64) ? 256 : kSlabMaxThreads; }
+// Threads per CTA: the register transforms and the W-step sweeps need the
+// 255-register budget of two warps per scheduler (nine warps would put three
+// on one scheduler and cap a thread at 168 registers); tubes beyond the thread
+// count loop.
+__host__ __device__ constexpr int slab_max_threads(int) { return 256; }
 
 // Odd stride between tubes in the slab (n3 values per tube).
 __host__ __device__ inline int slab_stride(int n3) { return n3 | 1; }
@@ -72,10 +71,11 @@ __host__ __device__ inline SlabLayout slab_layout(int n2, int n3, bool specialis
 //   forward   d_j = a_j d_{j-1} + b_j,   a_j = rho2 inv_j,  b_j = v_j inv_j
 //   backward  w_j = c_j w_{j+1} + d_j,   c_j = rho2 inv_j (0 at j = n2-1)
 // with a_j = c_j = 0, b_j = v_j at observed entries.  On return the row
-// holds W.  row[j] is at col[j * LP].  The row is processed 16 entries at a
-// time (half a mask word): the entries are read into registers first, so
-// only the multiply-add chain stays on the critical path.  The run start entering
-// each word is saved by the forward sweep for the backward one.
+// holds W.  row[j] is at col[j * LP].  The row is processed one mask word
+// (32 entries) at a time: the entries are read into registers first and the
+// table indices come from the mask bits, so only the multiply-add chain stays
+// on the critical path.  The run start entering each word is saved by the
+// forward sweep for the backward one.
 //
 // wtab: [6][n2] inv1, inv0 (runs starting at j = 0 / j > 0), c1 = rho2 inv1,
 //       c0 = rho2 inv0, e1, e0 (inverse pivot when the run ends at j = n2-1)
@@ -105,77 +105,86 @@ __host__ __device__ inline void wstep_tables(T* w, int n2, double mu, double rho
   }
 }
 
+// One mask word (32 entries, fewer in the last word) of the forward sweep.
+// rs: the start of the run holding j, from the mask bits below j or, when
+// there are none in this word, the run start st_w entering the word; so every
+// table index is known without the recurrence, and the recurrence itself is
+// one fused multiply-add per entry (a_j = 0, b_j = v_j at observed entries).
+template <typename T, bool FULL>
+__device__ __forceinline__ void wstep_fwd_word(T* __restrict__ col, int LP, uint32_t mw, int w, int qn, int st_w,
+                                               int n2, T rho2, const T* __restrict__ wtab, T& d) {
+  const int base = 32 * w;
+  T v[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (FULL || q < qn) v[q] = col[(base + q) * LP];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    if (FULL || q < qn) {
+      const int j = base + q;
+      const bool ob = (mw >> q) & 1u;
+      const uint32_t below = mw & ((1u << q) - 1u);
+      const int rs = below ? base + 32 - __clz(below) : st_w;
+      const T inv = wtab[((rs == 0) ? 0 : n2) + ((j == n2 - 1) ? 4 * n2 : 0) + (j - rs)];
+      d = fma(ob ? T(0) : rho2 * inv, d, ob ? v[q] : v[q] * inv);
+      v[q] = d;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (FULL || q < qn) col[(base + q) * LP] = v[q];
+}
+
+// One mask word of the backward sweep (c_j = 0 at observed entries and at
+// j = n2 - 1; observed slots already hold G).
+template <typename T, bool FULL>
+__device__ __forceinline__ void wstep_bwd_word(T* __restrict__ col, int LP, uint32_t mw, int w, int qn, int st_w,
+                                               int n2, const T* __restrict__ wtab, T& wn) {
+  const int base = 32 * w;
+  T v[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (FULL || q < qn) v[q] = col[(base + q) * LP];
+#pragma unroll
+  for (int q = 31; q >= 0; --q) {
+    if (FULL || q < qn) {
+      const int j = base + q;
+      const bool ob = (mw >> q) & 1u;
+      const uint32_t below = mw & ((1u << q) - 1u);
+      const int rs = below ? base + 32 - __clz(below) : st_w;
+      const T c = wtab[((rs == 0) ? 2 * n2 : 3 * n2) + (j - rs)];
+      wn = fma((ob || j == n2 - 1) ? T(0) : c, wn, v[q]);
+      v[q] = wn;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (FULL || q < qn) col[(base + q) * LP] = v[q];
+}
+
 template <typename T>
 __device__ void wstep_sweeps(T* __restrict__ col, int LP, const uint32_t* __restrict__ rowm, int* __restrict__ rowst,
                              int n2, T rho2, const T* __restrict__ wtab) {
-  constexpr int CH = 16;  // entries held in registers at a time (half a mask word)
   const int words = (n2 + 31) >> 5;
   // ---- forward: d_j = a_j d_{j-1} + b_j --------------------------------------
   T d = T(0);
-  int st = 0;  // start index of the current run of missing entries
+  int st = 0;  // start of the run of missing entries entering the word
   for (int w = 0; w < words; ++w) {
     const uint32_t mw = rowm[w];
+    const int qn = min(32, n2 - 32 * w);
     rowst[w] = st;
-#pragma unroll
-    for (int h = 0; h < 32 / CH; ++h) {
-      const int base = 32 * w + CH * h;
-      const int qn = min(CH, n2 - base);
-      T v[CH];
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (q < qn) v[q] = col[(base + q) * LP];
-#pragma unroll
-      for (int q = 0; q < CH; ++q) {
-        if (q < qn) {
-          const int j = base + q;
-          if ((mw >> (CH * h + q)) & 1u) {
-            d = v[q];
-            st = j + 1;
-          } else {
-            const T inv = wtab[((st == 0) ? 0 : n2) + ((j == n2 - 1) ? 4 * n2 : 0) + (j - st)];
-            d = fma(rho2 * inv, d, v[q] * inv);
-            v[q] = d;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (q < qn) col[(base + q) * LP] = v[q];
-    }
+    if (qn == 32) wstep_fwd_word<T, true>(col, LP, mw, w, qn, st, n2, rho2, wtab, d);
+    else wstep_fwd_word<T, false>(col, LP, mw, w, qn, st, n2, rho2, wtab, d);
+    const uint32_t m = (qn == 32) ? mw : (mw & ((1u << qn) - 1u));
+    if (m) st = 32 * w + 32 - __clz(m);
   }
-  // ---- backward: w_j = c_j w_{j+1} + d_j (observed slots already hold G) -----
+  // ---- backward: w_j = c_j w_{j+1} + d_j ---------------------------------------
   T wn = T(0);
   for (int w = words - 1; w >= 0; --w) {
     const uint32_t mw = rowm[w];
-    const int stw = rowst[w];
-#pragma unroll
-    for (int h = 32 / CH - 1; h >= 0; --h) {
-      const int base = 32 * w + CH * h;
-      const int qn = min(CH, n2 - base);  // may be <= 0 in the last word
-      T v[CH];
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (q < qn) v[q] = col[(base + q) * LP];
-#pragma unroll
-      for (int q = CH - 1; q >= 0; --q) {
-        if (q < qn) {
-          const int j = base + q;
-          const int b = CH * h + q;  // bit of j in the word
-          if ((mw >> b) & 1u) {
-            wn = v[q];
-          } else {
-            const uint32_t below = mw & ((1u << b) - 1u);
-            const int rs = below ? 32 * w + 32 - __clz(below) : stw;  // start of the run holding j
-            const T c = (j < n2 - 1) ? wtab[((rs == 0) ? 2 * n2 : 3 * n2) + (j - rs)] : T(0);
-            wn = fma(c, wn, v[q]);
-            v[q] = wn;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (q < qn) col[(base + q) * LP] = v[q];
-    }
+    const int qn = min(32, n2 - 32 * w);
+    if (qn == 32) wstep_bwd_word<T, true>(col, LP, mw, w, qn, rowst[w], n2, wtab, wn);
+    else wstep_bwd_word<T, false>(col, LP, mw, w, qn, rowst[w], n2, wtab, wn);
   }
 }
 
@@ -225,8 +234,8 @@ __device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, 
 // MODE_W   : W = iDFT(Z~ + R~); optional copy to Wout (column-major), partial
 //            sums ||W||^2 and ||K unfold(W,2)||^2.
 // MODE_R   : R = iDFT(R~); partial sums ||R||^2 and ||P_Omega R||^2.
-// Layouts used here: G row-major [i1][n3][n2] and mask words tube-major
-// [i1][n2][ceil(n3/32)] (written by k_pack).
+// Layouts used here: G row-major [i1][n3][n2] and mask words row-major
+// [i1][n3][ceil(n2/32)] (written by k_pack), copied to shared memory.
 // ---------------------------------------------------------------------------
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(slab_max_threads(L), 1)
@@ -237,7 +246,6 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   const int n3 = (L > 0) ? L : d.n3;
   const int S = n3 / 2 + 1;
   const int LP = slab_stride(n3);
-  const int lw = d.words;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (L > 0 && d.n3 != L) {
     if (tid == 0) set_err(d.err, DEV_BAD_LAUNCH);
@@ -255,23 +263,21 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   const cx<T>* zrow = d.Zt + (size_t)i1 * S * n2;
   const cx<T>* rrow = d.Rt + (size_t)i1 * S * n2;
   const T* Gi = d.G + (size_t)i1 * n2 * n3;
-  const uint32_t* Mi = d.mask + (size_t)i1 * n2 * lw;
+  const int mwords = d.mw;
+  const uint32_t* Mi = d.mask + (size_t)i1 * n3 * mwords;
   const bool wsolve = (MODE == MODE_ITER) && !init && d.rho2 != T(0);
   const T zfac = init ? T(0) : ((d.rho2 == T(0)) ? T(1) / (T(1) + d.mu) : T(1));
 
-  const int mwords = (n2 + 31) >> 5;
-  if (wsolve) {
+  if (wsolve)
     for (int j = tid; j < 6 * n2; j += nt) wtab[j] = d.winv[j];
-    if (L == 0) {
-      for (int j = tid; j < n3 * mwords; j += nt) msk[j] = 0u;
-      __syncthreads();
-    }
+  if (MODE != MODE_W) {
+    for (int j = tid; j < n3 * mwords; j += nt) msk[j] = __ldg(Mi + j);
+    __syncthreads();
   }
 
   // ---- phase A: inverse transform of each tube; v = G on the mask ------------
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
-    constexpr int LW = (L + 31) / 32;
     if (MODE == MODE_ITER) {
       // G (row-major, read coalesced) is staged into the slab, transposed to the
       // tube-major layout, with asynchronous copies issued ahead of the transforms;
@@ -314,17 +320,11 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       T x[L];
       fft::irfft<T, L>(X, x);
       if (MODE == MODE_ITER) {
-        uint32_t mw[LW];
-#pragma unroll
-        for (int w = 0; w < LW; ++w) mw[w] = act ? __ldg(Mi + (size_t)t * LW + w) : 0u;
+        const int ta = act ? t : 0;
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-          const bool ob = (mw[l >> 5] >> (l & 31)) & 1u;
-          if (wsolve) {
-            const uint32_t row_bits = __ballot_sync(0xffffffffu, ob);
-            if ((tid & 31) == 0) msk[l * mwords + (t >> 5)] = row_bits;
-          }
-          x[l] = ob ? spat[(size_t)(act ? t : 0) * LP + l] : x[l] * zfac;
+          const bool ob = act && ((msk[l * mwords + (ta >> 5)] >> (ta & 31)) & 1u);
+          x[l] = ob ? spat[(size_t)ta * LP + l] : x[l] * zfac;
         }
       }
       if (act) {
@@ -348,14 +348,9 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       T* col = spat + (size_t)t * LP;
       generic_irdft<T>(spec + t, n2, col, n3, d.twg);
       if (MODE == MODE_ITER) {
-        for (int w = 0; w < lw; ++w) {
-          const uint32_t mw = __ldg(Mi + (size_t)t * lw + w);
-          for (int q = 0; q < 32 && 32 * w + q < n3; ++q) {
-            const int l = 32 * w + q;
-            const bool ob = (mw >> q) & 1u;
-            if (wsolve && ob) atomicOr(msk + l * mwords + (t >> 5), 1u << (t & 31));
-            col[l] = ob ? __ldg(Gi + (size_t)l * n2 + t) : col[l] * zfac;
-          }
+        for (int l = 0; l < n3; ++l) {
+          const bool ob = (msk[l * mwords + (t >> 5)] >> (t & 31)) & 1u;
+          col[l] = ob ? __ldg(Gi + (size_t)l * n2 + t) : col[l] * zfac;
         }
       }
     }
@@ -376,7 +371,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
         }
         if (Wout) Wout[(size_t)i1 + (size_t)n1 * ((size_t)j + (size_t)n2 * l)] = v;
       } else {
-        if ((__ldg(Mi + (size_t)j * lw + (l >> 5)) >> (l & 31)) & 1u) b += (double)v * (double)v;
+        if ((msk[l * mwords + (j >> 5)] >> (j & 31)) & 1u) b += (double)v * (double)v;
       }
     }
     block_sum2(a, b, red);

@@ -1,0 +1,290 @@
+// Slab kernel with the mode-3 transforms in shared memory: one CTA per mode-1
+// index i1 (one OD pair), n3 = 2 M with M = N1 N2, and many threads per tube.
+//
+// The real transform of length n3 runs as a complex transform of length M on
+// the packed even/odd samples z_m = x_{2m} + i x_{2m+1} (Eq. (bar BA-k),
+// Eq. (barAAk); the half spectrum of Eq. (rcm_3-k+2) is all that is stored).
+// The length-M transform is split into two passes of small DFTs held in
+// registers (Cooley-Tukey with M = N1 N2):
+//   inverse: DFT_N1 over the stride-N2 slots, twiddle, DFT_N2 over contiguous
+//            groups; the spatial value z_m, m = k1 + N1 k2, lands in slot
+//            N2 k1 + k2 (a fixed permutation of each tube);
+//   forward: the same two passes in reverse order take that permuted order
+//            back to the natural order of the spectrum.
+// The W-step acts on the rows (i1, :, i3) one by one, so it works in the
+// permuted order unchanged: row i3 sits at offset slab_f_off(i3) of every tube.
+// Every pass is a loop over independent (group, tube) items with the tube
+// index fastest, so a warp reads one slot of 32 tubes (odd tube stride: no
+// bank conflicts) and shares its twiddle index; the code of each pass is one
+// small DFT, which keeps the instruction footprint small.
+//
+//   MODE_ITER  A1 split of the half spectrum of Z~ (written by k_ystep);
+//              A2/A3 inverse passes; v = G on the mask, Z elsewhere;
+//              W-step sweeps (Eq. (subquKKT)); C1/C2 forward passes;
+//              C3 split and R~ = W~ - Z~ stored.
+//   MODE_W     W = iDFT(Z~ + R~): optional copy to Wout (column-major),
+//              partial sums ||W||^2 and ||K unfold(W,2)||^2.
+//   MODE_R     R = iDFT(R~): partial sums ||R||^2 and ||P_Omega R||^2.
+#pragma once
+
+namespace tc {
+
+constexpr int kSlabFThreads = 512;
+
+// Floats between consecutive tubes: odd, and room for the M + 1 complex values
+// of the half spectrum.
+__host__ __device__ constexpr int slab_f_stride(int L) { return (L + 2) | 1; }
+
+struct SlabFLayout {
+  size_t msk, stw, wtab, red, buf, total;  // byte offsets and total shared bytes
+};
+
+template <typename T>
+__host__ __device__ inline SlabFLayout slab_f_layout(int n2, int L) {
+  SlabFLayout Lo{};
+  const size_t mw = (size_t)(n2 + 31) / 32;
+  size_t off = 0;
+  Lo.msk = off;  // row mask words [L][mw]
+  off = align_up(off + 4 * (size_t)L * mw, 16);
+  Lo.stw = off;  // W-step run starts per row and word
+  off = align_up(off + 4 * (size_t)L * mw, 16);
+  Lo.wtab = off;
+  off = align_up(off + sizeof(T) * 6 * (size_t)n2, 16);
+  Lo.red = off;
+  off = align_up(off + sizeof(double) * 2 * (kSlabFThreads / 32), 16);
+  Lo.buf = off;  // [n2][slab_f_stride(L)]
+  off = align_up(off + sizeof(T) * (size_t)n2 * slab_f_stride(L), 16);
+  Lo.total = off;
+  return Lo;
+}
+
+// Float offset of spatial index l (0 <= l < 2 N1 N2) inside a tube after the
+// inverse passes.
+template <int N1, int N2>
+__device__ __forceinline__ int slab_f_off(int l) {
+  const int m = l >> 1;
+  return 2 * (N2 * (m % N1) + m / N1) + (l & 1);
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> ld_slot(const T* tb, int slot) {
+  return cx<T>{tb[2 * slot], tb[2 * slot + 1]};
+}
+template <typename T>
+__device__ __forceinline__ void st_slot(T* tb, int slot, cx<T> v) {
+  tb[2 * slot] = v.re;
+  tb[2 * slot + 1] = v.im;
+}
+
+// One entry of the packed sequence for the inverse real transform:
+// z_k = E + i O, E = (a + conj b)/2, O = (a - conj b)/2 * w_L^{-k}, with
+// a = X[k], b = X[M - k].
+template <typename T, int L>
+__device__ __forceinline__ cx<T> inv_split(cx<T> a, cx<T> b, int k) {
+  const cx<T> bc = conj(b);
+  const cx<T> E = (a + bc) * T(0.5);
+  const cx<T> D = (a - bc) * T(0.5);
+  const cx<T> O = (k == 0) ? D : cmul(D, fft::tw<T, L, true>(k));
+  return cx<T>{E.re - O.im, E.im + O.re};
+}
+
+// X[k] of the forward real transform from Z[k] and Z[M - k] of the packed
+// transform (0 < k < M): E + O w_L^k, E = (Z_k + conj Z_{M-k})/2,
+// O = (Z_k - conj Z_{M-k}) / (2i).
+template <typename T, int L>
+__device__ __forceinline__ cx<T> fwd_split(cx<T> zk, cx<T> zm, int k) {
+  const cx<T> zc = conj(zm);
+  const cx<T> E = (zk + zc) * T(0.5);
+  const cx<T> D = (zk - zc) * T(0.5);
+  const cx<T> O = {D.im, -D.re};
+  return E + cmul(O, fft::tw<T, L, false>(k));
+}
+
+template <typename T, int L, int N1, int N2, int MODE>
+__global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __restrict__ Wout, int, int init) {
+  constexpr int M = L / 2;
+  static_assert(L % 2 == 0 && M == N1 * N2, "n3 = 2 N1 N2");
+  constexpr int LP = slab_f_stride(L);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int i1 = blockIdx.x;
+  const int n1 = d.n1, n2 = d.n2, mw = d.mw;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (d.n3 != L) {
+    if (tid == 0) set_err(d.err, DEV_BAD_LAUNCH);
+    return;
+  }
+  const SlabFLayout lay = slab_f_layout<T>(n2, L);
+  uint32_t* msk = reinterpret_cast<uint32_t*>(smem + lay.msk);
+  int* stw = reinterpret_cast<int*>(smem + lay.stw);
+  T* wtab = reinterpret_cast<T*>(smem + lay.wtab);
+  double* red = reinterpret_cast<double*>(smem + lay.red);
+  T* buf = reinterpret_cast<T*>(smem + lay.buf);
+  const cx<T>* zrow = d.Zt + (size_t)i1 * (M + 1) * n2;
+  const cx<T>* rrow = d.Rt + (size_t)i1 * (M + 1) * n2;
+  const T* Gi = d.G + (size_t)i1 * L * n2;
+  const bool wsolve = (MODE == MODE_ITER) && !init && d.rho2 != T(0);
+  const T zfac = init ? T(0) : ((d.rho2 == T(0)) ? T(1) / (T(1) + d.mu) : T(1));
+
+  if (MODE != MODE_W)
+    for (int j = tid; j < L * mw; j += nt) msk[j] = __ldg(d.mask + (size_t)i1 * L * mw + j);
+  if (wsolve)
+    for (int j = tid; j < 6 * n2; j += nt) wtab[j] = d.winv[j];
+
+  // ---- A1: half spectrum -> packed sequence z (pairs k, M - k) -----------------------
+  for (int e = tid; e < (M / 2 + 1) * n2; e += nt) {
+    const int k = e / n2, t = e - k * n2;
+    const int kc = M - k;
+    cx<T> a, b;
+    if (MODE == MODE_ITER) {
+      a = ldg_cx(zrow + (size_t)k * n2 + t);
+      b = ldg_cx(zrow + (size_t)kc * n2 + t);
+    } else if (MODE == MODE_W) {
+      a = ldg_cx(zrow + (size_t)k * n2 + t) + ldg_cx(rrow + (size_t)k * n2 + t);
+      b = ldg_cx(zrow + (size_t)kc * n2 + t) + ldg_cx(rrow + (size_t)kc * n2 + t);
+    } else {
+      a = ldg_cx(rrow + (size_t)k * n2 + t);
+      b = ldg_cx(rrow + (size_t)kc * n2 + t);
+    }
+    T* tb = buf + (size_t)t * LP;
+    if (k == 0) {  // DC and Nyquist slices are real
+      a.im = T(0);
+      b.im = T(0);
+    }
+    st_slot(tb, k, inv_split<T, L>(a, b, k));
+    if (k != 0 && k != kc) st_slot(tb, kc, inv_split<T, L>(b, a, kc));
+  }
+  __syncthreads();
+
+  // ---- A2: inverse DFT_N1 over slots N2 n1 + q, twiddle w_M^{-q k1} ------------------------
+  for (int e = tid; e < N2 * n2; e += nt) {
+    const int q = e / n2, t = e - q * n2;
+    T* tb = buf + (size_t)t * LP;
+    cx<T> v[N1], o[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
+    fft::CFFT<T, N1, L, true>::run(v, 1, o);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const cx<T> x = (k1 == 0) ? o[0] : cmul(o[k1], fft::tw<T, L, true>(2 * q * k1));
+      st_slot(tb, N2 * k1 + q, x);
+    }
+  }
+  __syncthreads();
+
+  // ---- A3: inverse DFT_N2 over slots N2 k1 + j -> spatial values; v = G on the mask -------
+  const T scale = T(1) / T(M);
+  for (int e = tid; e < N1 * n2; e += nt) {
+    const int k1 = e / n2, t = e - k1 * n2;
+    T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
+    T g[2 * N2];
+    if (MODE == MODE_ITER) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int l = 2 * (k1 + N1 * k2);
+        g[2 * k2] = __ldg(Gi + (size_t)l * n2 + t);
+        g[2 * k2 + 1] = __ldg(Gi + (size_t)(l + 1) * n2 + t);
+      }
+    }
+    cx<T> v[N2], o[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
+    fft::CFFT<T, N2, L, true>::run(v, 1, o);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      T x0 = o[k2].re * scale, x1 = o[k2].im * scale;
+      if (MODE == MODE_ITER) {
+        const int l = 2 * (k1 + N1 * k2);
+        const uint32_t w0 = msk[l * mw + (t >> 5)], w1 = msk[(l + 1) * mw + (t >> 5)];
+        x0 = ((w0 >> (t & 31)) & 1u) ? g[2 * k2] : x0 * zfac;
+        x1 = ((w1 >> (t & 31)) & 1u) ? g[2 * k2 + 1] : x1 * zfac;
+      }
+      tb[2 * k2] = x0;
+      tb[2 * k2 + 1] = x1;
+    }
+  }
+  __syncthreads();
+
+  // ---- partial sums of the read-back modes ----------------------------------------------
+  if (MODE == MODE_W || MODE == MODE_R) {
+    double a = 0.0, b = 0.0;
+    for (int e = tid; e < L * n2; e += nt) {
+      const int l = e / n2, t = e - l * n2;
+      const int off = slab_f_off<N1, N2>(l);
+      const T v = buf[(size_t)t * LP + off];
+      a += (double)v * (double)v;
+      if (MODE == MODE_W) {
+        if (t + 1 < n2) {
+          const double dv = (double)v - (double)buf[(size_t)(t + 1) * LP + off];
+          b += dv * dv;
+        }
+        if (Wout) Wout[(size_t)i1 + (size_t)n1 * ((size_t)t + (size_t)n2 * l)] = v;
+      } else {
+        if ((msk[l * mw + (t >> 5)] >> (t & 31)) & 1u) b += (double)v * (double)v;
+      }
+    }
+    block_sum2(a, b, red);
+    if (tid == 0) {
+      const int o = (MODE == MODE_W) ? 2 : 0;
+      d.part[(size_t)i1 * 4 + o] = a;
+      d.part[(size_t)i1 * 4 + o + 1] = b;
+    }
+    return;
+  }
+
+  // ---- W-step (one thread per row) ---------------------------------------------------------
+  if (wsolve) {
+    for (int l = tid; l < L; l += nt)
+      wstep_sweeps<T>(buf + slab_f_off<N1, N2>(l), LP, msk + l * mw, stw + l * mw, n2, d.rho2, wtab);
+    __syncthreads();
+  }
+
+  // ---- C1: forward DFT_N2 over slots N2 k1 + j, twiddle w_M^{k1 q} -----------------------
+  for (int e = tid; e < N1 * n2; e += nt) {
+    const int k1 = e / n2, t = e - k1 * n2;
+    T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
+    cx<T> v[N2], o[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
+    fft::CFFT<T, N2, L, false>::run(v, 1, o);
+#pragma unroll
+    for (int q = 0; q < N2; ++q) {
+      const cx<T> x = (q == 0) ? o[0] : cmul(o[q], fft::tw<T, L, false>(2 * k1 * q));
+      st_slot(tb, q, x);
+    }
+  }
+  __syncthreads();
+
+  // ---- C2: forward DFT_N1 over slots N2 k1 + q -> natural order -----------------------------
+  for (int e = tid; e < N2 * n2; e += nt) {
+    const int q = e / n2, t = e - q * n2;
+    T* tb = buf + (size_t)t * LP;
+    cx<T> v[N1], o[N1];
+#pragma unroll
+    for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
+    fft::CFFT<T, N1, L, false>::run(v, 1, o);
+#pragma unroll
+    for (int j = 0; j < N1; ++j) st_slot(tb, N2 * j + q, o[j]);
+  }
+  __syncthreads();
+
+  // ---- C3: split to the half spectrum; R~ = W~ - Z~ ------------------------------------------
+  cx<T>* rt = d.Rt + (size_t)i1 * (M + 1) * n2;
+  for (int e = tid; e < (M / 2 + 1) * n2; e += nt) {
+    const int k = e / n2, t = e - k * n2;
+    const int kc = M - k;
+    const T* tb = buf + (size_t)t * LP;
+    const size_t ok = (size_t)k * n2 + t, oc = (size_t)kc * n2 + t;
+    const cx<T> zk0 = ldg_cx(zrow + ok), zc0 = ldg_cx(zrow + oc);
+    if (k == 0) {
+      const cx<T> z0 = ld_slot(tb, 0);
+      rt[ok] = cx<T>{z0.re + z0.im, T(0)} - cx<T>{zk0.re, T(0)};
+      rt[oc] = cx<T>{z0.re - z0.im, T(0)} - cx<T>{zc0.re, T(0)};
+    } else {
+      const cx<T> zk = ld_slot(tb, k), zm = ld_slot(tb, kc);
+      rt[ok] = fwd_split<T, L>(zk, zm, k) - zk0;
+      if (k != kc) rt[oc] = fwd_split<T, L>(zm, zk, kc) - zc0;
+    }
+  }
+}
+
+}  // namespace tc

@@ -37,9 +37,26 @@ inline void slab_table(SlabFn<T> f[3]) {
   f[MODE_R] = k_slab<T, L, MODE_R>;
 }
 
-// Register-FFT lengths instantiated per precision (defined per translation unit).
+template <typename T, int L, int N1, int N2>
+inline void slab_f_table(SlabFn<T> f[3]) {
+  f[MODE_ITER] = k_slab_f<T, L, N1, N2, MODE_ITER>;
+  f[MODE_W] = k_slab_f<T, L, N1, N2, MODE_W>;
+  f[MODE_R] = k_slab_f<T, L, N1, N2, MODE_R>;
+}
+
+// Launch configuration of the slab kernel.
 template <typename T>
-bool pick_slab(int n3, SlabFn<T> f[3]);
+struct SlabCfg {
+  SlabFn<T> f[3];
+  int threads;
+  size_t smem;
+};
+
+// Slab kernels specialised for the tube length n3, instantiated per precision
+// (defined per translation unit); false when none applies to (n2, n3) within
+// the shared-memory limit optin.
+template <typename T>
+bool pick_slab(int n2, int n3, int optin, SlabCfg<T>& cfg);
 
 template <typename T>
 using YFn = void (*)(Dev<T>);
@@ -99,7 +116,7 @@ class Engine final : public EngineBase {
     n3_ = (int)p.n3;
     r_ = p.r;
     S_ = n3_ / 2 + 1;
-    words_ = (n3_ + 31) / 32;  // mask words per tube
+    mw_ = (n2_ + 31) / 32;  // mask words per row
     rp_ = pad_rank<T>(r_);
     const size_t N = (size_t)n1_ * n2_ * n3_;
     TC_CUDA_TRY(cudaGetDevice(&device_));
@@ -111,7 +128,7 @@ class Engine final : public EngineBase {
     // ---- state buffers -----------------------------------------------------------
     const size_t nx = (size_t)S_ * r_ * n1_, ny = (size_t)S_ * r_ * n2_, nrr = (size_t)S_ * r_ * r_;
     T* Gint = alloc<T>(N, err);
-    uint32_t* maskbits = alloc<uint32_t>((size_t)n1_ * n2_ * words_, err);
+    uint32_t* maskbits = alloc<uint32_t>((size_t)n1_ * n3_ * mw_, err);
     cx<T>* Rt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
     cx<T>* Zt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
     const int ytiles = (n2_ + 31) / 32;
@@ -131,21 +148,27 @@ class Engine final : public EngineBase {
     if (!err.empty()) return TC_ERR_NOMEM;
 
     // ---- kernel variants and shared memory -------------------------------------------
-    specialised_ = pick_slab<T>(n3_, slab_);
-    if (!specialised_) slab_table<T, 0>(slab_);
-    slab_threads_ = specialised_ ? std::min((n2_ + 31) / 32 * 32, slab_max_threads(n3_)) : 256;
-    slab_threads_ = std::max(slab_threads_, std::min(256, (n3_ + 31) / 32 * 32));  // one thread per W-step row
-    SlabLayout lay = slab_layout<T>(n2_, n3_, specialised_, true);
-    slabs_in_smem_ = lay.total <= (size_t)optin;
-    if (!slabs_in_smem_) {
-      lay = slab_layout<T>(n2_, n3_, specialised_, false);
-      T* scratch = alloc<T>(lay.slab_bytes / sizeof(T) * (size_t)n1_ + 16, err);
-      if (!err.empty()) return TC_ERR_NOMEM;
-      d_.scratch = scratch;
+    SlabCfg<T> cfg{};
+    specialised_ = pick_slab<T>(n2_, n3_, optin, cfg);
+    d_.scratch = nullptr;
+    if (specialised_) {
+      for (int m = 0; m < 3; ++m) slab_[m] = cfg.f[m];
+      slab_threads_ = cfg.threads;
+      slab_smem_ = cfg.smem;
+      slabs_in_smem_ = true;
     } else {
-      d_.scratch = nullptr;
+      slab_table<T, 0>(slab_);
+      slab_threads_ = 256;
+      SlabLayout lay = slab_layout<T>(n2_, n3_, false, true);
+      slabs_in_smem_ = lay.total <= (size_t)optin;
+      if (!slabs_in_smem_) {
+        lay = slab_layout<T>(n2_, n3_, false, false);
+        T* scratch = alloc<T>(lay.slab_bytes / sizeof(T) * (size_t)n1_ + 16, err);
+        if (!err.empty()) return TC_ERR_NOMEM;
+        d_.scratch = scratch;
+      }
+      slab_smem_ = lay.total;
     }
-    slab_smem_ = lay.total;
     for (int m = 0; m < 3; ++m)
       TC_CUDA_TRY(cudaFuncSetAttribute(slab_[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab_smem_));
 
@@ -201,7 +224,7 @@ class Engine final : public EngineBase {
     d_.n3 = n3_;
     d_.S = S_;
     d_.r = r_;
-    d_.words = words_;
+    d_.mw = mw_;
     d_.mu = (T)p.mu;
     d_.rho1 = (T)p.rho1;
     d_.rho2 = (T)p.rho2;
@@ -250,7 +273,7 @@ class Engine final : public EngineBase {
         return TC_ERR_NOMEM;
       }
     }
-    k_pack<T><<<n1_ * n2_, 256, 0, stream_>>>(dG, dM, Gint, maskbits, n1_, n2_, n3_, words_);
+    k_pack<T><<<n1_ * n3_, 256, 0, stream_>>>(dG, dM, Gint, maskbits, n1_, n2_, n3_, mw_);
     const int fgrid = 4 * 152;
     k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dY, Yt, n2_, r_, n3_, 1);
     if (dX) {
@@ -485,7 +508,7 @@ class Engine final : public EngineBase {
   cudaStream_t cap_stream_ = nullptr;
   cudaGraphExec_t graph_exec_ = nullptr;
   int device_ = 0;
-  int n1_ = 0, n2_ = 0, n3_ = 0, r_ = 0, S_ = 0, words_ = 0, rp_ = 8;
+  int n1_ = 0, n2_ = 0, n3_ = 0, r_ = 0, S_ = 0, mw_ = 0, rp_ = 8;
   bool poisoned_ = false;
   bool specialised_ = false;
   bool slabs_in_smem_ = true;

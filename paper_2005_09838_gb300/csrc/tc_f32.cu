@@ -1,17 +1,17 @@
-// FP32 engine: generic slab kernel here; the register-FFT slab kernels live in
-// their own translation units (compiled in parallel).
+// FP32 engine: generic slab kernel here; the slab kernels specialised for a
+// tube length live in their own translation units (compiled in parallel).
 #include "tc_engine.cuh"
 
 namespace tc {
 
-bool slab_setup_f32_112(SlabFn<float> f[3]);
-bool slab_setup_f32_168(SlabFn<float> f[3]);
+bool slab_setup_f32_112(int n2, int optin, SlabCfg<float>& cfg);
+bool slab_setup_f32_168(int n2, int optin, SlabCfg<float>& cfg);
 
 template <>
-bool pick_slab<float>(int n3, SlabFn<float> f[3]) {
+bool pick_slab<float>(int n2, int n3, int optin, SlabCfg<float>& cfg) {
   switch (n3) {
-    case 112: return slab_setup_f32_112(f);
-    case 168: return slab_setup_f32_168(f);
+    case 112: return slab_setup_f32_112(n2, optin, cfg);
+    case 168: return slab_setup_f32_168(n2, optin, cfg);
     default: return false;
   }
 }

@@ -4,11 +4,15 @@
 namespace tc {
 
 template <>
-bool pick_slab<double>(int n3, SlabFn<double> f[3]) {
-  switch (n3) {
-    case 7: slab_table<double, 7>(f); return true;
-    default: return false;
-  }
+bool pick_slab<double>(int n2, int n3, int optin, SlabCfg<double>& cfg) {
+  if (n3 != 7) return false;
+  const SlabLayout lay = slab_layout<double>(n2, 7, true, true);
+  if (lay.total > (size_t)optin) return false;
+  slab_table<double, 7>(cfg.f);
+  // one thread per tube (up to the register budget) and at least one per W-step row
+  cfg.threads = std::max(std::min((n2 + 31) / 32 * 32, slab_max_threads(7)), 32);
+  cfg.smem = lay.total;
+  return true;
 }
 
 template <>

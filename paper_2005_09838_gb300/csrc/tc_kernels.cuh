@@ -9,8 +9,8 @@
 //
 // Layouts (last index fastest):
 //   G    [n1][n3][n2]  real, observed values (0 off the mask), row-major
-//   mask [n1][n2][words] words = ceil(n3/32); bit i3 % 32 of word i3 / 32 of
-//                        tube (i1, i2) = entry (i1, i2, i3) observed
+//   mask [n1][n3][mw]  mw = ceil(n2/32); bit i2 % 32 of word i2 / 32 of
+//                        row (i1, :, i3) = entry (i1, i2, i3) observed
 //   Rt   [n1][S][n2]   complex
 //   Xt   [S][r][n1]    complex
 //   Yt   [S][r][n2]    complex
@@ -26,7 +26,7 @@ namespace tc {
 
 template <typename T>
 struct Dev {
-  int n1, n2, n3, S, r, words;
+  int n1, n2, n3, S, r, mw;
   T mu, rho1, rho2;
   const T* G;
   const uint32_t* mask;
@@ -96,5 +96,6 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 }  // namespace tc
 
 #include "k_slab.cuh"
+#include "k_slab_f.cuh"
 #include "k_slice.cuh"
 #include "k_aux.cuh"

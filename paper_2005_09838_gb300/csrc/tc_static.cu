@@ -122,7 +122,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
-  const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, words = (n3 + 31) / 32;
+  const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, mw = (n2 + 31) / 32;
   const int rp = pad_rank<T>(r);
   const size_t N = (size_t)n1 * n2 * n3;
   const size_t nx = (size_t)S * r * n1, ny = (size_t)S * r * n2, nrr = (size_t)S * r * r;
@@ -141,7 +141,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   Carve cv{base};
   Dev<T> d{};
   T* Gint = cv.take<T>(N);
-  uint32_t* maskbits = cv.take<uint32_t>((size_t)n1 * n2 * words);
+  uint32_t* maskbits = cv.take<uint32_t>((size_t)n1 * n3 * mw);
   d.Rt = cv.take<cx<T>>((size_t)n1 * S * n2);
   d.Zt = cv.take<cx<T>>((size_t)n1 * S * n2);
   d.ytiles = (n2 + 31) / 32;
@@ -169,7 +169,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   d.n3 = n3;
   d.S = S;
   d.r = r;
-  d.words = words;
+  d.mw = mw;
   d.mu = (T)p.mu;
   d.rho1 = (T)p.rho1;
   d.rho2 = (T)p.rho2;
@@ -195,7 +195,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   // the array keeps the previous call's contents: clear what must start at zero
   cudaMemsetAsync(d.err, 0, sizeof(int), st);
   k_static_tables<T><<<3, 256, 0, st>>>(winv, hinv, twg, n1, n2, n3, p.mu, p.rho1, p.rho2);
-  k_pack<T><<<n1 * n2, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, words);
+  k_pack<T><<<n1 * n3, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, mw);
   k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(Y0), d.Yt, n2, r, n3, 1);
   if (X0) {
     k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(X0), d.Xt, n1, r, n3, 0);
