@@ -106,14 +106,17 @@ __host__ __device__ inline void wstep_tables(T* w, int n2, double mu, double rho
 }
 
 // One mask word (32 entries, fewer in the last word) of the forward sweep.
-// rs: the start of the run holding j, from the mask bits below j or, when
-// there are none in this word, the run start st_w entering the word; so every
-// table index is known without the recurrence, and the recurrence itself is
-// one fused multiply-add per entry (a_j = 0, b_j = v_j at observed entries).
-template <typename T, bool FULL>
+// The table index of entry j is inv-table + (j - rs), rs the start of the run
+// holding j: from the mask bits below j (rs = 32 w + 32 - clz(below)) or,
+// when there are none in this word, the run start st_w entering the word, so
+// every index is known without the recurrence; the recurrence itself is one
+// fused multiply-add per entry (a_j = 0, b_j = v_j at observed entries).
+// LAST: the word holds j = n2 - 1 (the e-table pivot there).
+template <typename T, bool FULL, bool LAST>
 __device__ __forceinline__ void wstep_fwd_word(T* __restrict__ col, int LP, uint32_t mw, int w, int qn, int st_w,
                                                int n2, T rho2, const T* __restrict__ wtab, T& d) {
   const int base = 32 * w;
+  const int cw = ((st_w == 0) ? 0 : n2) + base - st_w;  // index base of entries without bits below
   T v[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q)
@@ -121,11 +124,11 @@ __device__ __forceinline__ void wstep_fwd_word(T* __restrict__ col, int LP, uint
 #pragma unroll
   for (int q = 0; q < 32; ++q) {
     if (FULL || q < qn) {
-      const int j = base + q;
       const bool ob = (mw >> q) & 1u;
       const uint32_t below = mw & ((1u << q) - 1u);
-      const int rs = below ? base + 32 - __clz(below) : st_w;
-      const T inv = wtab[((rs == 0) ? 0 : n2) + ((j == n2 - 1) ? 4 * n2 : 0) + (j - rs)];
+      int idx = below ? (n2 - 32 + q + __clz(below)) : (cw + q);
+      if (LAST && base + q == n2 - 1) idx += 4 * n2;
+      const T inv = wtab[idx];
       d = fma(ob ? T(0) : rho2 * inv, d, ob ? v[q] : v[q] * inv);
       v[q] = d;
     }
@@ -135,12 +138,14 @@ __device__ __forceinline__ void wstep_fwd_word(T* __restrict__ col, int LP, uint
     if (FULL || q < qn) col[(base + q) * LP] = v[q];
 }
 
-// One mask word of the backward sweep (c_j = 0 at observed entries and at
-// j = n2 - 1; observed slots already hold G).
-template <typename T, bool FULL>
+// One mask word of the backward sweep: c_j = rho2 inv_j at table index
+// 2 n2 + (forward index), 0 at observed entries and at j = n2 - 1 (observed
+// slots already hold G).
+template <typename T, bool FULL, bool LAST>
 __device__ __forceinline__ void wstep_bwd_word(T* __restrict__ col, int LP, uint32_t mw, int w, int qn, int st_w,
                                                int n2, const T* __restrict__ wtab, T& wn) {
   const int base = 32 * w;
+  const int cw = ((st_w == 0) ? 2 * n2 : 3 * n2) + base - st_w;
   T v[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q)
@@ -148,12 +153,12 @@ __device__ __forceinline__ void wstep_bwd_word(T* __restrict__ col, int LP, uint
 #pragma unroll
   for (int q = 31; q >= 0; --q) {
     if (FULL || q < qn) {
-      const int j = base + q;
       const bool ob = (mw >> q) & 1u;
       const uint32_t below = mw & ((1u << q) - 1u);
-      const int rs = below ? base + 32 - __clz(below) : st_w;
-      const T c = wtab[((rs == 0) ? 2 * n2 : 3 * n2) + (j - rs)];
-      wn = fma((ob || j == n2 - 1) ? T(0) : c, wn, v[q]);
+      const int idx = below ? (3 * n2 - 32 + q + __clz(below)) : (cw + q);
+      const T c = wtab[idx];
+      const bool zero = ob || (LAST && base + q == n2 - 1);
+      wn = fma(zero ? T(0) : c, wn, v[q]);
       v[q] = wn;
     }
   }
@@ -166,26 +171,31 @@ template <typename T>
 __device__ void wstep_sweeps(T* __restrict__ col, int LP, const uint32_t* __restrict__ rowm, int* __restrict__ rowst,
                              int n2, T rho2, const T* __restrict__ wtab) {
   const int words = (n2 + 31) >> 5;
+  const int ql = n2 - 32 * (words - 1);  // entries in the last word
   // ---- forward: d_j = a_j d_{j-1} + b_j --------------------------------------
   T d = T(0);
   int st = 0;  // start of the run of missing entries entering the word
-  for (int w = 0; w < words; ++w) {
+  for (int w = 0; w < words - 1; ++w) {
     const uint32_t mw = rowm[w];
-    const int qn = min(32, n2 - 32 * w);
     rowst[w] = st;
-    if (qn == 32) wstep_fwd_word<T, true>(col, LP, mw, w, qn, st, n2, rho2, wtab, d);
-    else wstep_fwd_word<T, false>(col, LP, mw, w, qn, st, n2, rho2, wtab, d);
-    const uint32_t m = (qn == 32) ? mw : (mw & ((1u << qn) - 1u));
-    if (m) st = 32 * w + 32 - __clz(m);
+    wstep_fwd_word<T, true, false>(col, LP, mw, w, 32, st, n2, rho2, wtab, d);
+    if (mw) st = 32 * w + 32 - __clz(mw);
+  }
+  {
+    const int w = words - 1;
+    rowst[w] = st;
+    if (ql == 32) wstep_fwd_word<T, true, true>(col, LP, rowm[w], w, 32, st, n2, rho2, wtab, d);
+    else wstep_fwd_word<T, false, true>(col, LP, rowm[w], w, ql, st, n2, rho2, wtab, d);
   }
   // ---- backward: w_j = c_j w_{j+1} + d_j ---------------------------------------
   T wn = T(0);
-  for (int w = words - 1; w >= 0; --w) {
-    const uint32_t mw = rowm[w];
-    const int qn = min(32, n2 - 32 * w);
-    if (qn == 32) wstep_bwd_word<T, true>(col, LP, mw, w, qn, rowst[w], n2, wtab, wn);
-    else wstep_bwd_word<T, false>(col, LP, mw, w, qn, rowst[w], n2, wtab, wn);
+  {
+    const int w = words - 1;
+    if (ql == 32) wstep_bwd_word<T, true, true>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
+    else wstep_bwd_word<T, false, true>(col, LP, rowm[w], w, ql, rowst[w], n2, wtab, wn);
   }
+  for (int w = words - 2; w >= 0; --w)
+    wstep_bwd_word<T, true, false>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
 }
 
 // ---------------------------------------------------------------------------

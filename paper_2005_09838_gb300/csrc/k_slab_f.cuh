@@ -131,21 +131,37 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
     for (int j = tid; j < 6 * n2; j += nt) wtab[j] = d.winv[j];
 
   // ---- A1: half spectrum -> packed sequence z (pairs k, M - k) -----------------------
+  if (MODE != MODE_W) {
+    // the half spectrum lands in slots 0..M of every tube through asynchronous
+    // copies (all in flight at once), then is split in place
+    const cx<T>* src = (MODE == MODE_ITER) ? zrow : rrow;
+    int k = tid / n2, t = tid - (tid / n2) * n2;
+    for (int e = tid; e < (M + 1) * n2; e += nt) {
+      const T* g = reinterpret_cast<const T*>(src + e);
+      T* dst = buf + (size_t)t * LP + 2 * k;
+      cp_async_elem(dst, g);
+      cp_async_elem(dst + 1, g + 1);
+      t += nt;
+      while (t >= n2) {
+        t -= n2;
+        ++k;
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
   for (int e = tid; e < (M / 2 + 1) * n2; e += nt) {
     const int k = e / n2, t = e - k * n2;
     const int kc = M - k;
+    T* tb = buf + (size_t)t * LP;
     cx<T> a, b;
-    if (MODE == MODE_ITER) {
-      a = ldg_cx(zrow + (size_t)k * n2 + t);
-      b = ldg_cx(zrow + (size_t)kc * n2 + t);
-    } else if (MODE == MODE_W) {
+    if (MODE == MODE_W) {
       a = ldg_cx(zrow + (size_t)k * n2 + t) + ldg_cx(rrow + (size_t)k * n2 + t);
       b = ldg_cx(zrow + (size_t)kc * n2 + t) + ldg_cx(rrow + (size_t)kc * n2 + t);
     } else {
-      a = ldg_cx(rrow + (size_t)k * n2 + t);
-      b = ldg_cx(rrow + (size_t)kc * n2 + t);
+      a = ld_slot(tb, k);
+      b = ld_slot(tb, kc);
     }
-    T* tb = buf + (size_t)t * LP;
     if (k == 0) {  // DC and Nyquist slices are real
       a.im = T(0);
       b.im = T(0);
@@ -172,18 +188,27 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   __syncthreads();
 
   // ---- A3: inverse DFT_N2 over slots N2 k1 + j -> spatial values; v = G on the mask -------
+  // (the G values of the next item are loaded while the current one is computed)
   const T scale = T(1) / T(M);
+  T gn[2 * N2];
+  auto load_g = [&](int e) {
+    const int k1 = e / n2, t = e - k1 * n2;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int l = 2 * (k1 + N1 * k2);
+      gn[2 * k2] = __ldg(Gi + (size_t)l * n2 + t);
+      gn[2 * k2 + 1] = __ldg(Gi + (size_t)(l + 1) * n2 + t);
+    }
+  };
+  if (MODE == MODE_ITER && tid < N1 * n2) load_g(tid);
   for (int e = tid; e < N1 * n2; e += nt) {
     const int k1 = e / n2, t = e - k1 * n2;
     T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
     T g[2 * N2];
     if (MODE == MODE_ITER) {
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        const int l = 2 * (k1 + N1 * k2);
-        g[2 * k2] = __ldg(Gi + (size_t)l * n2 + t);
-        g[2 * k2 + 1] = __ldg(Gi + (size_t)(l + 1) * n2 + t);
-      }
+      for (int q = 0; q < 2 * N2; ++q) g[q] = gn[q];
+      if (e + nt < N1 * n2) load_g(e + nt);
     }
     cx<T> v[N2], o[N2];
 #pragma unroll

@@ -9,19 +9,26 @@ namespace tc {
 // (Lemma "SVPMPI": A^+ = V diag(1/lambda) V^* over the eigenvalues above the
 // cutoff rtol * lambda_max).
 //
-// Fast path (block-wide): Gauss-Jordan inverse without pivoting (stable for
-// Hermitian positive definite A), accepted only when ||A||_1 ||A^-1||_1 <
-// 1/(10 rtol) (1-norms bounded above through |re| + |im|), which certifies
-// lambda_min > rtol * lambda_max: no eigenvalue is cut, A^+ = A^-1 and the
-// projector A A^+ is exactly I.  Otherwise warp 0 runs a cyclic Jacobi
-// eigendecomposition that applies the cutoff rule literally.
+// Fast path: Gauss-Jordan inverse without pivoting (stable for Hermitian
+// positive definite A), accepted only when a bound on lambda_max/lambda_min
+// stays below a fraction of 1/rtol, which certifies lambda_min > rtol *
+// lambda_max: no eigenvalue is cut, A^+ = A^-1 and the projector A A^+ is
+// exactly I.  r <= 16: one warp with the matrix in registers, bound
+// ||A||_F ||A^-1||_F < 1/(2 rtol) (lambda_max <= ||A||_F, 1/lambda_min =
+// ||A^-1||_2 <= ||A^-1||_F; at that size the computed inverse is within a
+// few percent of the true one).  Larger r: the block, bound
+// ||A||_1 ||A^-1||_1 < 1/(10 rtol) (1-norms bounded through |re| + |im|).
+// Otherwise warp 0 runs a parallel cyclic Jacobi eigendecomposition
+// (round-robin pairs, r/2 rotations at a time) that applies the cutoff rule
+// literally.
 //
 // A, Ap, P, V: r*r row-major complex values in shared memory; W: 2*r*r work;
-// piv: 3*r complex values; sred: 2 values.  Every thread of the block must
+// piv: 3*r complex values; sred: 4 values.  Every thread of the block must
 // call it.  Returns (block-uniform) 1 if the inverse path was taken.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, int r, T rtol);
+__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+                                        T rtol);
 
 template <typename T>
 __device__ inline T warp_norm1_bound(const cx<T>* M, int ld, int col0, int r) {
@@ -55,75 +62,165 @@ __device__ __forceinline__ T tiny_pivot() {
   return sizeof(T) == 8 ? T(1e-300) : T(1e-37f);
 }
 
-template <typename T>
-__device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
-                                      int r, T rtol) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int n2c = 2 * r;  // augmented columns [A | I], row-major r x 2r
+// Gauss-Jordan on W = [A | I] (r x 2r, row-major) by the threads [t0, t0 + nt)
+// of the caller; sync() orders the steps among them.  Returns 0 when a pivot
+// is not positive.
+template <typename T, typename Sync>
+__device__ __forceinline__ int gauss_jordan(cx<T>* W, cx<T>* piv, int r, int t, int nt, Sync sync) {
+  const int n2c = 2 * r;
   cx<T>* colp = piv;
   cx<T>* rowp = piv + r;
-  for (int e = tid; e < r * n2c; e += nt) {
-    const int i = e / n2c, j = e - i * n2c;
-    W[e] = (j < r) ? A[i * r + j] : cx<T>{(j - r == i) ? T(1) : T(0), T(0)};
-  }
-  if (tid < 32) {
-    const T an = warp_norm1_bound(A, r, 0, r);
-    if (tid == 0) sred[0] = an;
-  }
-  __syncthreads();
-  const T anorm = sred[0];
-  int ok = (anorm > T(0)) && isfinite(anorm);
-  for (int p = 0; p < r && ok; ++p) {
+  for (int p = 0; p < r; ++p) {
     const T pv = W[p * n2c + p].re;
-    if (!((pv > tiny_pivot<T>()) && isfinite(pv))) {
-      ok = 0;
-      break;
-    }
+    if (!((pv > tiny_pivot<T>()) && isfinite(pv))) return 0;
     const T ip = rcp_refined(pv);
-    for (int e = tid; e < r + n2c; e += nt) {
+    for (int e = t; e < r + n2c; e += nt) {
       if (e < r) colp[e] = W[e * n2c + p];
       else rowp[e - r] = W[p * n2c + (e - r)] * ip;
     }
-    __syncthreads();
-    for (int e = tid; e < r * n2c; e += nt) {
+    sync();
+    for (int e = t; e < r * n2c; e += nt) {
       const int i = e / n2c, j = e - i * n2c;
       W[e] = (i == p) ? rowp[j] : W[e] - cmul(colp[i], rowp[j]);
     }
-    __syncthreads();
+    sync();
   }
-  if (ok) {
+  return 1;
+}
+
+// Gauss-Jordan inverse of the Hermitian r x r matrix A (r <= RP <= 16) by one
+// warp with [A | I] in registers: lane j holds column j of the 2r augmented
+// columns, and the pivot column reaches the other lanes by shuffles.  On
+// success (return 1) Ainv (row-major r x r) holds A^-1 and an, in the
+// Frobenius norms of A and A^-1; 0 when a pivot is not positive.
+template <typename T, int RP>
+__device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in) {
+  const int lane = threadIdx.x & 31;
+  cx<T> c[RP];
+#pragma unroll
+  for (int i = 0; i < RP; ++i) {
+    cx<T> v = {T(0), T(0)};
+    if (i < r) {
+      if (lane < r) v = A[i * r + lane];
+      else if (lane == r + i) v = cx<T>{T(1), T(0)};
+    }
+    c[i] = v;
+  }
+  T cs = T(0);
+#pragma unroll
+  for (int i = 0; i < RP; ++i) cs += c[i].re * c[i].re + c[i].im * c[i].im;
+  an = T(0);
+  in = T(0);
+  T a = (lane < r) ? cs : T(0);
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  an = sqrt(a);
+  if (!(a > T(0) && isfinite(a))) return 0;
+#pragma unroll
+  for (int p = 0; p < RP; ++p) {
+    if (p >= r) break;
+    const T pv = __shfl_sync(0xffffffffu, c[p].re, p);
+    if (!((pv > tiny_pivot<T>()) && isfinite(pv))) return 0;
+    const T ip = rcp_refined(pv);
+    const cx<T> rp = c[p] * ip;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) {
+      const cx<T> cp = {__shfl_sync(0xffffffffu, c[i].re, p), __shfl_sync(0xffffffffu, c[i].im, p)};
+      c[i] = (i == p) ? rp : c[i] - cmul(cp, rp);
+    }
+  }
+  cs = T(0);
+#pragma unroll
+  for (int i = 0; i < RP; ++i) cs += c[i].re * c[i].re + c[i].im * c[i].im;
+  a = (lane >= r && lane < 2 * r) ? cs : T(0);
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  in = sqrt(a);
+  if (lane >= r && lane < 2 * r) {
+#pragma unroll
+    for (int i = 0; i < RP; ++i)
+      if (i < r) Ainv[i * r + (lane - r)] = c[i];
+  }
+  __syncwarp();
+  return 1;
+}
+
+template <typename T, int RP>
+__device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
+                                      int r, T rtol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int ok;
+  if constexpr (RP <= 16) {
+    // W receives A^-1 (row-major r x r)
     if (tid < 32) {
-      const T in = warp_norm1_bound(W, n2c, r, r);
-      if (tid == 0) sred[1] = in;
+      T an, in;
+      const int g = warp_gj_inverse<T, RP>(A, W, r, an, in);
+      if (tid == 0) sred[1] = (g && isfinite(in) && an * in < T(0.5) / rtol) ? T(1) : T(0);
     }
     __syncthreads();
-    const T inorm = sred[1];
-    ok = isfinite(inorm) && (anorm * inorm < T(0.1) / rtol);
-  }
-  if (ok) {
-    for (int e = tid; e < r * r; e += nt) {
-      const int i = e / r, j = e - i * r;
-      // symmetrise: A^-1 of a Hermitian matrix is Hermitian
-      const cx<T> a = W[i * n2c + r + j];
-      const cx<T> b = W[j * n2c + r + i];
-      Ap[e] = cx<T>{T(0.5) * (a.re + b.re), T(0.5) * (a.im - b.im)};
-      P[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
+    ok = sred[1] != T(0);
+    if (ok) {
+      for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e - i * r;
+        // symmetrise: A^-1 of a Hermitian matrix is Hermitian
+        const cx<T> a = W[i * r + j];
+        const cx<T> b = W[j * r + i];
+        Ap[e] = cx<T>{T(0.5) * (a.re + b.re), T(0.5) * (a.im - b.im)};
+        P[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
+      }
+      __syncthreads();
+      return 1;
+    }
+  } else {
+    const int n2c = 2 * r;  // augmented columns [A | I], row-major r x 2r
+    for (int e = tid; e < r * n2c; e += nt) {
+      const int i = e / n2c, j = e - i * n2c;
+      W[e] = (j < r) ? A[i * r + j] : cx<T>{(j - r == i) ? T(1) : T(0), T(0)};
+    }
+    if (tid < 32) {
+      const T an = warp_norm1_bound(A, r, 0, r);
+      if (tid == 0) sred[0] = an;
     }
     __syncthreads();
-    return 1;
+    const T anorm = sred[0];
+    ok = (anorm > T(0)) && isfinite(anorm);
+    if (ok) ok = gauss_jordan<T>(W, piv, r, tid, nt, []() { __syncthreads(); });
+    if (tid < 32) {
+      const T in = ok ? warp_norm1_bound(W, n2c, r, r) : T(0);
+      if (tid == 0) sred[1] = (ok && isfinite(in) && anorm * in < T(0.1) / rtol) ? T(1) : T(0);
+    }
+    __syncthreads();
+    ok = sred[1] != T(0);
+    if (ok) {
+      for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e - i * r;
+        const cx<T> a = W[i * n2c + r + j];
+        const cx<T> b = W[j * n2c + r + i];
+        Ap[e] = cx<T>{T(0.5) * (a.re + b.re), T(0.5) * (a.im - b.im)};
+        P[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
+      }
+      __syncthreads();
+      return 1;
+    }
   }
   __syncthreads();
-  if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, r, rtol);
+  if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol);
   __syncthreads();
   return 0;
 }
 
-// Cyclic complex Jacobi eigendecomposition A = V diag(lambda) V^* by one warp,
-// then A^+ and P = A A^+ with the cutoff rule.
+// Parallel cyclic complex Jacobi eigendecomposition A = V diag(lambda) V^* by
+// one warp, then A^+ and P = A A^+ with the cutoff rule.  Each round rotates
+// the disjoint pairs of a round-robin schedule (m - 1 rounds of m/2 pairs,
+// m = r rounded up to even, index r a dummy when r is odd); a rotation is
+// skipped when |a_pq| <= 4 u max(|a_pp|, |a_qq|) (u the unit roundoff), and
+// the sweeps stop after one without rotations.
 template <typename T>
-__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, int r, T rtol) {
+__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+                                        T rtol) {
   const int lane = threadIdx.x & 31;
-  // ---- cyclic Jacobi on a copy of A (stored in W, row-major r x r) ----------
+  const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
+  const int m = (r + 1) & ~1, np = m / 2;
+  // rotation of pair k: piv[2k] = (cs, sn), piv[2k + 1] = unit phase u; rows p, q in rpq
+  int* rpq = reinterpret_cast<int*>(piv + 2 * np);  // 2 ints per pair (fits in the third r values)
   __syncwarp();
   for (int e = lane; e < r * r; e += 32) {
     W[e] = A[e];
@@ -131,49 +228,79 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
     V[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
   }
   __syncwarp();
-  T fro = T(0);
-  for (int e = lane; e < r * r; e += 32) fro += W[e].re * W[e].re + W[e].im * W[e].im;
-  for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
-  // converged when the off-diagonal mass is below (unit roundoff)^2 of the total
-  const T tol = (sizeof(T) == 8 ? T(1e-30) : T(1e-14f)) * fro + tiny_pivot<T>();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    T off = T(0);
-    for (int e = lane; e < r * r; e += 32) {
-      const int i = e / r, j = e - i * r;
-      if (i != j) off += W[e].re * W[e].re + W[e].im * W[e].im;
-    }
-    for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
-    if (off <= tol) break;
-    for (int p = 0; p < r - 1; ++p) {
-      for (int q = p + 1; q < r; ++q) {
-        const cx<T> c = W[p * r + q];
-        const T ac = hypot(c.re, c.im);
-        if (ac <= tiny_pivot<T>()) continue;
-        const T a = W[p * r + p].re, b = W[q * r + q].re;
-        const cx<T> u = {c.re / ac, c.im / ac};
-        const T tau = (b - a) / (T(2) * ac);
-        const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-        const T cs = T(1) / sqrt(T(1) + t * t), sn = t * cs;
-        __syncwarp();
-        // columns: A J with J = [[cs, sn u], [-sn conj(u), cs]]
-        for (int i = lane; i < r; i += 32) {
-          const cx<T> aip = W[i * r + p], aiq = W[i * r + q];
-          W[i * r + p] = aip * cs - cmulc(aiq, u) * sn;
-          W[i * r + q] = cmul(aip, u) * sn + aiq * cs;
-          const cx<T> vip = V[i * r + p], viq = V[i * r + q];
-          V[i * r + p] = vip * cs - cmulc(viq, u) * sn;
-          V[i * r + q] = cmul(vip, u) * sn + viq * cs;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    bool any = false;
+    for (int round = 0; round < m - 1; ++round) {
+      // ---- rotations of this round (lane k < np) ----
+      bool rot = false;
+      if (lane < np) {
+        int a, b;
+        if (lane == 0) {
+          a = round;
+          b = m - 1;
+        } else {
+          a = (round + lane) % (m - 1);
+          b = (round - lane + m - 1) % (m - 1);
         }
-        __syncwarp();
-        // rows: J^H (A J)
-        for (int j = lane; j < r; j += 32) {
-          const cx<T> apj = W[p * r + j], aqj = W[q * r + j];
-          W[p * r + j] = apj * cs - cmul(aqj, u) * sn;
-          W[q * r + j] = cmulc(apj, u) * sn + aqj * cs;
+        const int p = min(a, b), q = max(a, b);
+        T cs = T(1), sn = T(0);
+        cx<T> uu = {T(1), T(0)};
+        if (q < r) {
+          const cx<T> c = W[p * r + q];
+          const T n2 = c.re * c.re + c.im * c.im;
+          const T app = W[p * r + p].re, aqq = W[q * r + q].re;
+          // below 4u max(|a_pp|, |a_qq|) the entry is at the rounding level of the
+          // rotations themselves (its effect on any eigenvalue is below u^2 lambda_max)
+          const T thr = T(4) * u_round * fmax(fabs(app), fabs(aqq));
+          if (n2 > tiny_pivot<T>() && n2 > thr * thr) {
+            const T iac = rsqrt(n2);
+            uu = cx<T>{c.re * iac, c.im * iac};
+            const T tau = (aqq - app) * T(0.5) * iac;
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            cs = rsqrt(T(1) + t * t);
+            sn = t * cs;
+            rot = true;
+          }
         }
-        __syncwarp();
+        piv[2 * lane] = cx<T>{cs, sn};
+        piv[2 * lane + 1] = uu;
+        rpq[2 * lane] = p;
+        rpq[2 * lane + 1] = (q < r) ? q : -1;
       }
+      rot = __any_sync(0xffffffffu, rot);
+      __syncwarp();
+      if (!rot) continue;
+      any = true;
+      // ---- columns: W J and V J (item = row i, pair k) ----
+      for (int e = lane; e < r * np; e += 32) {
+        const int k = e / r, i = e - k * r;
+        const int p = rpq[2 * k], q = rpq[2 * k + 1];
+        if (q < 0) continue;
+        const T cs = piv[2 * k].re, sn = piv[2 * k].im;
+        const cx<T> uu = piv[2 * k + 1];
+        // J = [[cs, sn u], [-sn conj(u), cs]] on columns p, q
+        const cx<T> aip = W[i * r + p], aiq = W[i * r + q];
+        W[i * r + p] = aip * cs - cmulc(aiq, uu) * sn;
+        W[i * r + q] = cmul(aip, uu) * sn + aiq * cs;
+        const cx<T> vip = V[i * r + p], viq = V[i * r + q];
+        V[i * r + p] = vip * cs - cmulc(viq, uu) * sn;
+        V[i * r + q] = cmul(vip, uu) * sn + viq * cs;
+      }
+      __syncwarp();
+      // ---- rows: J^H (W J) (item = pair k, column j) ----
+      for (int e = lane; e < r * np; e += 32) {
+        const int k = e / r, j = e - k * r;
+        const int p = rpq[2 * k], q = rpq[2 * k + 1];
+        if (q < 0) continue;
+        const T cs = piv[2 * k].re, sn = piv[2 * k].im;
+        const cx<T> uu = piv[2 * k + 1];
+        const cx<T> apj = W[p * r + j], aqj = W[q * r + j];
+        W[p * r + j] = apj * cs - cmul(aqj, uu) * sn;
+        W[q * r + j] = cmulc(apj, uu) * sn + aqj * cs;
+      }
+      __syncwarp();
     }
+    if (!any) break;
   }
   // eigenvalues on the diagonal; cutoff relative to lambda_max
   T lmax = T(0);
@@ -183,10 +310,10 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
   for (int e = lane; e < r * r; e += 32) {
     const int i = e / r, j = e - i * r;
     cx<T> sa = {T(0), T(0)}, sp = {T(0), T(0)};
-    for (int m = 0; m < r; ++m) {
-      const T lam = W[m * r + m].re;
+    for (int mm = 0; mm < r; ++mm) {
+      const T lam = W[mm * r + mm].re;
       if (lmax > T(0) && lam > cut) {
-        const cx<T> vv = cmulc(V[i * r + m], V[j * r + m]);  // V_im conj(V_jm)
+        const cx<T> vv = cmulc(V[i * r + mm], V[j * r + mm]);  // V_im conj(V_jm)
         sa = sa + vv * (T(1) / lam);
         sp = sp + vv;
       }
@@ -245,9 +372,10 @@ struct Log2<1> {
 
 // ---------------------------------------------------------------------------
 // Q_k = R~_k Y~_k^H (n1 x r per slice), the W~Y~^H part of the X-gradient of
-// Eq. (hkXYDer) that involves the residual.  Grid (S, ceil(n1/32)); one warp
-// per row with coalesced loads along the row, Y~_k staged in shared memory.
-// Reads R~ once.
+// Eq. (hkXYDer) that involves the residual.  Grid (S, ceil(n1/32)); a warp
+// takes one or two rows at a time with coalesced loads along the rows, four
+// 32-column loads per row in flight, Y~_k staged in shared memory.  Reads R~
+// once.
 // ---------------------------------------------------------------------------
 template <typename T, int RP>
 __global__ void __launch_bounds__(kSliceThreads) k_qcon(Dev<T> d, cx<T>* __restrict__ Qout) {
@@ -260,32 +388,64 @@ __global__ void __launch_bounds__(kSliceThreads) k_qcon(Dev<T> d, cx<T>* __restr
   for (int e = tid; e < r * n2; e += blockDim.x) Ys[e] = Y[e];
   __syncthreads();
   constexpr int HALF = (RP > 16) ? 16 : RP;  // complex values per reduction pass
-  for (int ii = wid; ii < 32; ii += nw) {
-    const int i = blockIdx.y * 32 + ii;
-    if (i >= n1) break;
-    const cx<T>* row = d.Rt + ((size_t)i * S + k) * n2;
-    cx<T> acc[RP];
+  constexpr int RR = (RP <= 8) ? 2 : 1;       // rows per pass of a warp
+  constexpr int U = 4;                        // 32-column loads in flight per row
+  for (int ii = wid * RR; ii < 32; ii += nw * RR) {
+    const cx<T>* rowp[RR];
+    bool live[RR];
 #pragma unroll
-    for (int s = 0; s < RP; ++s) acc[s] = cx<T>{T(0), T(0)};
-    for (int j = lane; j < n2; j += 32) {
-      const cx<T> v = ldg_cx(row + j);
+    for (int q = 0; q < RR; ++q) {
+      const int i = blockIdx.y * 32 + ii + q;
+      live[q] = i < n1;
+      rowp[q] = d.Rt + ((size_t)(live[q] ? i : 0) * S + k) * n2;
+    }
+    if (!live[0]) break;
+    cx<T> acc[RR][RP];
 #pragma unroll
-      for (int s = 0; s < RP; ++s)
-        if (s < r) cfmac(acc[s], v, Ys[(size_t)s * n2 + j]);
+    for (int q = 0; q < RR; ++q)
+#pragma unroll
+      for (int s = 0; s < RP; ++s) acc[q][s] = cx<T>{T(0), T(0)};
+    for (int j0 = 0; j0 < n2; j0 += 32 * U) {
+      cx<T> v[RR][U];
+#pragma unroll
+      for (int q = 0; q < RR; ++q)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + 32 * u + lane;
+          v[q][u] = (live[q] && j < n2) ? ldg_cx(rowp[q] + j) : cx<T>{T(0), T(0)};
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + 32 * u + lane;
+        if (j < n2) {
+#pragma unroll
+          for (int s = 0; s < RP; ++s)
+            if (s < r) {
+              const cx<T> y = Ys[(size_t)s * n2 + j];
+#pragma unroll
+              for (int q = 0; q < RR; ++q) cfmac(acc[q][s], v[q][u], y);
+            }
+        }
+      }
     }
 #pragma unroll
-    for (int h = 0; h < RP; h += HALF) {
-      T f[2 * HALF];
+    for (int q = 0; q < RR; ++q) {
+      if (!live[q]) continue;
+      const int i = blockIdx.y * 32 + ii + q;
 #pragma unroll
-      for (int s = 0; s < HALF; ++s) {
-        f[2 * s] = acc[h + s].re;
-        f[2 * s + 1] = acc[h + s].im;
+      for (int h = 0; h < RP; h += HALF) {
+        T f[2 * HALF];
+#pragma unroll
+        for (int s = 0; s < HALF; ++s) {
+          f[2 * s] = acc[q][h + s].re;
+          f[2 * s + 1] = acc[q][h + s].im;
+        }
+        const T tot = warp_reduce_scatter<T, 2 * HALF>(f);
+        const int idx = lane >> (5 - Log2<2 * HALF>::value);
+        const int s = h + idx / 2;
+        const bool first = (lane & ((32 >> Log2<2 * HALF>::value) - 1)) == 0;
+        if (first && s < r) reinterpret_cast<T*>(Qout + ((size_t)k * r + s) * n1 + i)[idx & 1] = tot;
       }
-      const T tot = warp_reduce_scatter<T, 2 * HALF>(f);
-      const int idx = lane >> (5 - Log2<2 * HALF>::value);
-      const int s = h + idx / 2;
-      const bool first = (lane & ((32 >> Log2<2 * HALF>::value) - 1)) == 0;
-      if (first && s < r) reinterpret_cast<T*>(Qout + ((size_t)k * r + s) * n1 + i)[idx & 1] = tot;
     }
   }
 }
@@ -331,6 +491,74 @@ __host__ __device__ inline XLayout xstep_layout(int n1, int n2, int r, bool arra
   return L;
 }
 
+// col <- H_rho1^{-1} col for H_rho1 = I + rho1 H^T H (tridiagonal, Eq. (KKTcondition)),
+// by one warp.  The LU sweeps are the first-order recurrences
+//   forward   y_i = a_i y_{i-1} + hinv_i b_i,   backward  x_i = a_i x_{i+1} + y_i,
+// a_i = rho1 hinv_i (hinv: inverse LU pivots), each evaluated as a parallel
+// prefix scan of affine maps over 32 segments of the column: every lane
+// composes its segment, a 5-step shuffle scan gives the value entering it,
+// and the lane then runs its segment.
+template <typename T>
+__device__ void warp_tridiag_solve(cx<T>* col, int n1, const T* __restrict__ hinv, const T* __restrict__ ha) {
+  const int lane = threadIdx.x & 31;
+  const int seg = (n1 + 31) >> 5;
+  const int i0 = min(lane * seg, n1), i1 = min(i0 + seg, n1);
+  // ---- forward ----
+  T A = T(1);
+  cx<T> B = {T(0), T(0)};
+  for (int i = i0; i < i1; ++i) {
+    const T a = ha[i], b = hinv[i];
+    const cx<T> v = col[i];
+    B = cx<T>{fma(a, B.re, v.re * b), fma(a, B.im, v.im * b)};
+    A *= a;
+  }
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const T Ap = __shfl_up_sync(0xffffffffu, A, dd);
+    const T Br = __shfl_up_sync(0xffffffffu, B.re, dd), Bi = __shfl_up_sync(0xffffffffu, B.im, dd);
+    if (lane >= dd) {
+      B = cx<T>{fma(A, Br, B.re), fma(A, Bi, B.im)};
+      A *= Ap;
+    }
+  }
+  cx<T> y = {__shfl_up_sync(0xffffffffu, B.re, 1), __shfl_up_sync(0xffffffffu, B.im, 1)};
+  if (lane == 0) y = cx<T>{T(0), T(0)};
+  for (int i = i0; i < i1; ++i) {
+    const T a = ha[i], b = hinv[i];
+    const cx<T> v = col[i];
+    y = cx<T>{fma(a, y.re, v.re * b), fma(a, y.im, v.im * b)};
+    col[i] = y;
+  }
+  __syncwarp();
+  // ---- backward (x_{n1} = 0) ----
+  A = T(1);
+  B = cx<T>{T(0), T(0)};
+  for (int i = i1 - 1; i >= i0; --i) {
+    const T a = ha[i];
+    const cx<T> v = col[i];
+    B = cx<T>{fma(a, B.re, v.re), fma(a, B.im, v.im)};
+    A *= a;
+  }
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    const T Ap = __shfl_down_sync(0xffffffffu, A, dd);
+    const T Br = __shfl_down_sync(0xffffffffu, B.re, dd), Bi = __shfl_down_sync(0xffffffffu, B.im, dd);
+    if (lane + dd < 32) {
+      B = cx<T>{fma(A, Br, B.re), fma(A, Bi, B.im)};
+      A *= Ap;
+    }
+  }
+  cx<T> x = {__shfl_down_sync(0xffffffffu, B.re, 1), __shfl_down_sync(0xffffffffu, B.im, 1)};
+  if (lane == 31) x = cx<T>{T(0), T(0)};
+  for (int i = i1 - 1; i >= i0; --i) {
+    const T a = ha[i];
+    const cx<T> v = col[i];
+    x = cx<T>{fma(a, x.re, v.re), fma(a, x.im, v.im)};
+    col[i] = x;
+  }
+  __syncwarp();
+}
+
 // (H^T H x)_i for the first-difference matrix H of Eq. (Toeplitz) on n1 entries:
 // deg_i x_i - x_{i-1} - x_{i+1} over the neighbours that exist.
 template <typename T>
@@ -342,7 +570,7 @@ __device__ __forceinline__ cx<T> hth_at(const cx<T>* x, int i, int n1) {
   return v;
 }
 
-template <typename T>
+template <typename T, int RP>
 __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = blockIdx.x;
@@ -404,7 +632,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
     }
   }
   __syncthreads();
-  const bool certA = block_pinv_herm<T>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol) != 0;
+  const bool certA = block_pinv_herm<T, RP>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol) != 0;
 
   // ---- B = Q A^+ - rho1 (H^T H X~) P ------------------------------------------------------
   for (int e = tid; e < r * n1; e += blockDim.x) {
@@ -423,48 +651,9 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
     Ts[e] = acc;
   }
   __syncthreads();
-  // ---- d_X = H_rho1^{-1} B: one column per thread, one FMA per step ---------------------
+  // ---- d_X = H_rho1^{-1} B: one warp per column --------------------------------------------
   if (rho1 != T(0) && n1 > 1) {
-    constexpr int CH = 16;  // values staged in registers per chunk
-    for (int s = tid; s < r; s += blockDim.x) {
-      cx<T>* col = Ts + (size_t)s * n1;
-      cx<T> y = {T(0), T(0)};
-      for (int i0 = 0; i0 < n1; i0 += CH) {
-        cx<T> v[CH];
-#pragma unroll
-        for (int q = 0; q < CH; ++q) v[q] = (i0 + q < n1) ? col[i0 + q] : cx<T>{T(0), T(0)};
-#pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          const int i = i0 + q;
-          if (i < n1) {
-            const T a = ha[i], b = hinv[i];
-            y = cx<T>{fma(a, y.re, v[q].re * b), fma(a, y.im, v[q].im * b)};
-            v[q] = y;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < CH; ++q)
-          if (i0 + q < n1) col[i0 + q] = v[q];
-      }
-      cx<T> x = col[n1 - 1];
-      for (int i1 = n1 - 2; i1 >= 0; i1 -= CH) {
-        cx<T> v[CH];
-#pragma unroll
-        for (int q = 0; q < CH; ++q) v[q] = (i1 - q >= 0) ? col[i1 - q] : cx<T>{T(0), T(0)};
-#pragma unroll
-        for (int q = 0; q < CH; ++q) {
-          const int i = i1 - q;
-          if (i >= 0) {
-            const T a = ha[i];
-            x = cx<T>{fma(a, x.re, v[q].re), fma(a, x.im, v[q].im)};
-            v[q] = x;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < CH; ++q)
-          if (i1 - q >= 0) col[i1 - q] = v[q];
-      }
-    }
+    for (int s = wid; s < r; s += nw) warp_tridiag_solve<T>(Ts + (size_t)s * n1, n1, hinv, ha);
     __syncthreads();
   }
   // ---- X~' = X~ + d_X (Ts; Xs keeps the old factor) ---------------------------------------
@@ -476,38 +665,52 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
   __syncthreads();
 
   // ---- G = X~'^H H_rho1 X~' (Hermitian) and Dg = E - G ----------------------------------
-  // (H X~')^H (H X~') = sum_i conj(x_i - x_{i+1}) (x_i - x_{i+1}) row by row
-  for (int task = wid; task < rr; task += nw) {
-    const int s = task / r, u = task - s * r;
-    const cx<T>* xs = Ts + (size_t)s * n1;
-    const cx<T>* xu = Ts + (size_t)u * n1;
-    const cx<T>* ou = Xs + (size_t)u * n1;
-    cx<T> a0 = {T(0), T(0)}, hh = {T(0), T(0)}, dd = {T(0), T(0)};
-    for (int i = lane; i < n1; i += 32) {
-      const cx<T> a = xs[i], b = xu[i];
-      cfmaconj(a0, a, b);
-      cfmaconj(dd, a, b - ou[i]);
-      if (i + 1 < n1) cfmaconj(hh, a - xs[i + 1], b - xu[i + 1]);
-    }
-    T f[8] = {a0.re, a0.im, hh.re, hh.im, dd.re, dd.im, T(0), T(0)};
-    const T tot = warp_reduce_scatter<T, 8>(f);  // lane l: value index l >> 2
-    const T h_re = __shfl_sync(0xffffffffu, tot, 8), h_im = __shfl_sync(0xffffffffu, tot, 12);
-    const T a_re = __shfl_sync(0xffffffffu, tot, 0), a_im = __shfl_sync(0xffffffffu, tot, 4);
-    const T d_re = __shfl_sync(0xffffffffu, tot, 16), d_im = __shfl_sync(0xffffffffu, tot, 20);
-    if (lane == 0) {
-      cx<T> dg = {-(d_re + rho1 * h_re), -(d_im + rho1 * h_im)};
-      if (realslice) dg.im = T(0);
-      Dgm[s * r + u] = dg;
-      if (s <= u) {
-        cx<T> g = {a_re + rho1 * h_re, a_im + rho1 * h_im};
-        if (s == u || realslice) g.im = T(0);
-        Gm[s * r + u] = g;
-        Gm[u * r + s] = cx<T>{g.re, -g.im};
+  // (H X~')^H (H X~') = sum_i conj(x_i - x_{i+1}) (x_i - x_{i+1}) row by row.
+  // tp adjacent threads share one (s, u) pair and split the rows; their partial
+  // sums are combined by shuffles in a fixed order.
+  {
+    int tp = 1;
+    while (tp < 32 && tp * 2 * rr <= (int)blockDim.x) tp *= 2;
+    const int per_pass = blockDim.x / tp;
+    for (int base = 0; base < rr; base += per_pass) {
+      const int task = base + tid / tp, q = tid & (tp - 1);
+      const bool has = task < rr;
+      const int s = has ? task / r : 0, u = has ? task - s * r : 0;
+      cx<T> a0 = {T(0), T(0)}, hh = {T(0), T(0)}, dd = {T(0), T(0)};
+      if (has) {
+        const cx<T>* xs = Ts + (size_t)s * n1;
+        const cx<T>* xu = Ts + (size_t)u * n1;
+        const cx<T>* ou = Xs + (size_t)u * n1;
+        for (int i = q; i < n1; i += tp) {
+          const cx<T> a = xs[i], b = xu[i];
+          cfmaconj(a0, a, b);
+          cfmaconj(dd, a, b - ou[i]);
+          if (i + 1 < n1) cfmaconj(hh, a - xs[i + 1], b - xu[i + 1]);
+        }
+      }
+      for (int o = tp >> 1; o > 0; o >>= 1) {
+        a0.re += __shfl_xor_sync(0xffffffffu, a0.re, o);
+        a0.im += __shfl_xor_sync(0xffffffffu, a0.im, o);
+        hh.re += __shfl_xor_sync(0xffffffffu, hh.re, o);
+        hh.im += __shfl_xor_sync(0xffffffffu, hh.im, o);
+        dd.re += __shfl_xor_sync(0xffffffffu, dd.re, o);
+        dd.im += __shfl_xor_sync(0xffffffffu, dd.im, o);
+      }
+      if (has && q == 0) {
+        cx<T> dg = {-(dd.re + rho1 * hh.re), -(dd.im + rho1 * hh.im)};
+        if (realslice) dg.im = T(0);
+        Dgm[s * r + u] = dg;
+        if (s <= u) {
+          cx<T> g = {a0.re + rho1 * hh.re, a0.im + rho1 * hh.im};
+          if (s == u || realslice) g.im = T(0);
+          Gm[s * r + u] = g;
+          Gm[u * r + s] = cx<T>{g.re, -g.im};
+        }
       }
     }
   }
   __syncthreads();
-  block_pinv_herm<T>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol);
+  block_pinv_herm<T, RP>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol);
   // ---- Dg and G^+ for k_ystep; X~ <- X~' ---------------------------------------------------
   for (int e = tid; e < rr; e += blockDim.x) {
     cx<T> gp = Ap[e];
@@ -519,121 +722,160 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
 }
 
 // ---------------------------------------------------------------------------
-// Y-step of slice k on a tile of 32 columns (step 2):
+// Y-step of slice k on a tile of TW = 32 CPL columns (step 2):
 //   D   = X~'^H R~_k(:, tile)       (contraction over n1; reads R~ once)
 //   Y~' = Y~ + G^+ (Dg Y~ + D)      (= Y~ - G^+ grad_Y, see k_xstep)
-// then the tile Gram of Y~' (A of the next X-step) and Z~ = X~'Y~' on the tile
-// (step 3, read by the slab kernel).
-// Grid (S, ceil(n2/32)); warp w accumulates rows i = w, w + 8, ...
+// then the Grams of Y~' over each 32 columns (A of the next X-step) and
+// Z~ = X~'Y~' on the tile (step 3, read by the slab kernel).
+// Grid (S, ceil(n2/TW)); warp w accumulates rows i = w, w + 8, ...; a lane
+// holds CPL columns (two for r <= 16, so each X~' value read from shared
+// memory feeds two columns).
 // ---------------------------------------------------------------------------
 constexpr int kYThreads = 256;
 
+__host__ __device__ constexpr int ystep_cpl(int rp) { return rp <= 16 ? 2 : 1; }
+
 template <typename T, int RP>
 __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
+  constexpr int CPL = ystep_cpl(RP), TW = 32 * CPL;
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = blockIdx.x;
-  const int j0 = blockIdx.y * 32;
+  const int j0 = blockIdx.y * TW;
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S, rr = r * r;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  cx<T>* red = reinterpret_cast<cx<T>*>(smem);  // [nw][RP][32]
-  cx<T>* Ds = red + nw * RP * 32;               // [RP][32]
-  cx<T>* Yo = Ds + RP * 32;                     // [RP][32]
-  cx<T>* Dgs = Yo + RP * 32;                    // [rr]
+  cx<T>* red = reinterpret_cast<cx<T>*>(smem);  // [nw][RP][TW]
+  cx<T>* Ds = red + nw * RP * TW;               // [RP][TW]
+  cx<T>* Yo = Ds + RP * TW;                     // [RP][TW]
+  cx<T>* Dgs = Yo + RP * TW;                    // [rr]
   cx<T>* Gh = Dgs + rr;                         // [rr]
-  cx<T>* Yn = Gh + rr;                          // [RP][32] the new Y~' of the tile
-  cx<T>* Xs = Yn + RP * 32;                     // [r][n1]
+  cx<T>* Yn = Gh + rr;                          // [RP][TW] the new Y~' of the tile
+  cx<T>* Xs = Yn + RP * TW;                     // [r][n1]
   const cx<T>* Xg = d.Xt + (size_t)k * r * n1;
   for (int e = tid; e < r * n1; e += blockDim.x) Xs[e] = Xg[e];
   for (int e = tid; e < rr; e += blockDim.x) {
     Dgs[e] = d.Dg[(size_t)k * rr + e];
     Gh[e] = d.Gp[(size_t)k * rr + e];
   }
-  for (int e = tid; e < r * 32; e += blockDim.x) {
-    const int s = e >> 5, c = e & 31;
-    Yo[s * 32 + c] = (j0 + c < n2) ? d.Yt[((size_t)k * r + s) * n2 + j0 + c] : cx<T>{T(0), T(0)};
+  for (int e = tid; e < r * TW; e += blockDim.x) {
+    const int s = e / TW, c = e - s * TW;
+    Yo[s * TW + c] = (j0 + c < n2) ? d.Yt[((size_t)k * r + s) * n2 + j0 + c] : cx<T>{T(0), T(0)};
   }
   __syncthreads();
-  const int j = j0 + lane;
-  cx<T> acc[RP];
+  cx<T> acc[CPL][RP];
 #pragma unroll
-  for (int s = 0; s < RP; ++s) acc[s] = cx<T>{T(0), T(0)};
-  if (j < n2) {
+  for (int h = 0; h < CPL; ++h)
+#pragma unroll
+    for (int s = 0; s < RP; ++s) acc[h][s] = cx<T>{T(0), T(0)};
+  bool live[CPL];
+#pragma unroll
+  for (int h = 0; h < CPL; ++h) live[h] = j0 + 32 * h + lane < n2;
+  const cx<T>* rbase = d.Rt + (size_t)k * n2 + j0 + lane;  // + i * S * n2 + 32 h
+  const size_t rstride = (size_t)S * n2;
+  {
     int i = wid;
-    for (; i + 3 * nw < n1; i += 4 * nw) {
-      cx<T> v[4];
+    for (; i + nw < n1; i += 2 * nw) {
+      cx<T> v[2][CPL];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = ldg_cx(d.Rt + ((size_t)(i + q * nw) * S + k) * n2 + j);
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+        for (int h = 0; h < CPL; ++h)
+          v[q][h] = live[h] ? ldg_cx(rbase + (size_t)(i + q * nw) * rstride + 32 * h) : cx<T>{T(0), T(0)};
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int s = 0; s < RP; ++s)
-          if (s < r) cfmaconj(acc[s], Xs[(size_t)s * n1 + i + q * nw], v[q]);
+          if (s < r) {
+            const cx<T> x = Xs[(size_t)s * n1 + i + q * nw];
+#pragma unroll
+            for (int h = 0; h < CPL; ++h) cfmaconj(acc[h][s], x, v[q][h]);
+          }
     }
     for (; i < n1; i += nw) {
-      const cx<T> v = ldg_cx(d.Rt + ((size_t)i * S + k) * n2 + j);
+      cx<T> v[CPL];
+#pragma unroll
+      for (int h = 0; h < CPL; ++h)
+        v[h] = live[h] ? ldg_cx(rbase + (size_t)i * rstride + 32 * h) : cx<T>{T(0), T(0)};
 #pragma unroll
       for (int s = 0; s < RP; ++s)
-        if (s < r) cfmaconj(acc[s], Xs[(size_t)s * n1 + i], v);
+        if (s < r) {
+          const cx<T> x = Xs[(size_t)s * n1 + i];
+#pragma unroll
+          for (int h = 0; h < CPL; ++h) cfmaconj(acc[h][s], x, v[h]);
+        }
     }
   }
 #pragma unroll
-  for (int s = 0; s < RP; ++s) red[(wid * RP + s) * 32 + lane] = acc[s];
+  for (int s = 0; s < RP; ++s)
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) red[(wid * RP + s) * TW + 32 * h + lane] = acc[h][s];
   __syncthreads();
   // V = Dg Y~ + D (= -grad_Y on the tile)
-  for (int e = tid; e < r * 32; e += blockDim.x) {
-    const int s = e >> 5, c = e & 31;
+  for (int e = tid; e < r * TW; e += blockDim.x) {
+    const int s = e / TW, c = e - s * TW;
     cx<T> v = {T(0), T(0)};
-    for (int w = 0; w < nw; ++w) v = v + red[(w * RP + s) * 32 + c];
-    for (int u = 0; u < r; ++u) cfma(v, Dgs[s * r + u], Yo[u * 32 + c]);
-    Ds[s * 32 + c] = v;
+    for (int w = 0; w < nw; ++w) v = v + red[(w * RP + s) * TW + c];
+    for (int u = 0; u < r; ++u) cfma(v, Dgs[s * r + u], Yo[u * TW + c]);
+    Ds[s * TW + c] = v;
   }
   __syncthreads();
   const bool realslice = (k == 0) || (2 * k == d.n3);
-  for (int e = tid; e < RP * 32; e += blockDim.x) {
-    const int s = e >> 5, c = e & 31;
+  for (int e = tid; e < RP * TW; e += blockDim.x) {
+    const int s = e / TW, c = e - s * TW;
     if (s >= r || j0 + c >= n2) {
       Yn[e] = cx<T>{T(0), T(0)};
       continue;
     }
     cx<T> y = Yo[e];
-    for (int u = 0; u < r; ++u) cfma(y, Gh[s * r + u], Ds[u * 32 + c]);
+    for (int u = 0; u < r; ++u) cfma(y, Gh[s * r + u], Ds[u * TW + c]);
     if (realslice) y.im = T(0);
     d.Yt[((size_t)k * r + s) * n2 + j0 + c] = y;
     Yn[e] = y;
   }
   __syncthreads();
 
-  // ---- Gram of the new Y~' over this tile (A of the next X-step) ----------------------
+  // ---- Grams of the new Y~' over each 32 columns (A of the next X-step) ----------------
   const int ntask = r * (r + 1) / 2;
-  for (int task = wid; task < ntask; task += nw) {
+  for (int t = wid; t < CPL * ntask; t += nw) {
+    const int h = t / ntask, task = t - h * ntask;
+    const int tile = blockIdx.y * CPL + h;
+    if (tile >= d.ytiles) continue;
     int s, u;
     tri_index(task, r, s, u);
     cx<T> g = {T(0), T(0)};
-    cfmac(g, Yn[s * 32 + lane], Yn[u * 32 + lane]);
+    cfmac(g, Yn[s * TW + 32 * h + lane], Yn[u * TW + 32 * h + lane]);
     g.re = warp_sum(g.re);
     g.im = warp_sum(g.im);
-    if (lane == 0) d.Ag[((size_t)k * d.ytiles + blockIdx.y) * ntask + task] = cx<double>{(double)g.re, (double)g.im};
+    if (lane == 0) d.Ag[((size_t)k * d.ytiles + tile) * ntask + task] = cx<double>{(double)g.re, (double)g.im};
   }
 
   // ---- Z~(:, tile, k) = X~' Y~'  (step 3, written for the slab kernel) ----------------
-  cx<T> yv[RP];
+  cx<T> yv[CPL][RP];
 #pragma unroll
-  for (int s = 0; s < RP; ++s) yv[s] = Yn[s * 32 + lane];
-  if (j < n2) {
-    cx<T>* zc = d.Zt + (size_t)k * n2 + j;
-    for (int i = wid; i < n1; i += nw) {
-      cx<T> z = {T(0), T(0)};
+  for (int h = 0; h < CPL; ++h)
 #pragma unroll
-      for (int s = 0; s < RP; ++s)
-        if (s < r) cfma(z, Xs[(size_t)s * n1 + i], yv[s]);
-      zc[(size_t)i * S * n2] = z;
-    }
+    for (int s = 0; s < RP; ++s) yv[h][s] = Yn[s * TW + 32 * h + lane];
+  cx<T>* zc = d.Zt + (size_t)k * n2 + j0 + lane;
+  for (int i = wid; i < n1; i += nw) {
+    cx<T> z[CPL];
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) z[h] = cx<T>{T(0), T(0)};
+#pragma unroll
+    for (int s = 0; s < RP; ++s)
+      if (s < r) {
+        const cx<T> x = Xs[(size_t)s * n1 + i];
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) cfma(z[h], x, yv[h][s]);
+      }
+#pragma unroll
+    for (int h = 0; h < CPL; ++h)
+      if (live[h]) zc[(size_t)i * rstride + 32 * h] = z[h];
   }
 }
 
 template <typename T>
 __host__ inline size_t ystep_smem_bytes(int n1, int r, int rp) {
-  return ((size_t)(kYThreads / 32 + 3) * rp * 32 + 2 * (size_t)r * r + (size_t)r * n1) * sizeof(cx<T>);
+  const size_t tw = 32 * (size_t)ystep_cpl(rp);
+  return ((size_t)(kYThreads / 32 + 3) * rp * tw + 2 * (size_t)r * r + (size_t)r * n1) * sizeof(cx<T>);
 }
 
 template <typename T>

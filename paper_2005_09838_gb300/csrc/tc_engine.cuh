@@ -80,6 +80,20 @@ inline YFn<T> pick_ystep(int rp) {
 }
 
 template <typename T>
+using XFn = void (*)(Dev<T>, const cx<T>*, int);
+
+template <typename T>
+inline XFn<T> pick_xstep(int rp) {
+  switch (rp) {
+    case 2: return k_xstep<T, 2>;
+    case 4: return k_xstep<T, 4>;
+    case 8: return k_xstep<T, 8>;
+    case 16: return k_xstep<T, 16>;
+    default: return k_xstep<T, 32>;
+  }
+}
+
+template <typename T>
 inline QFn<T> pick_qcon(int rp) {
   switch (rp) {
     case 2: return k_qcon<T, 2>;
@@ -180,7 +194,8 @@ class Engine final : public EngineBase {
       err = "X-step shared memory exceeds the device limit";
       return TC_ERR_UNSUPPORTED;
     }
-    TC_CUDA_TRY(cudaFuncSetAttribute(k_xstep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xstep_smem_));
+    xstep_ = pick_xstep<T>(rp_);
+    TC_CUDA_TRY(cudaFuncSetAttribute(xstep_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xstep_smem_));
     ystep_ = pick_ystep<T>(rp_);
     ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
     qcon_ = pick_qcon<T>(rp_);
@@ -452,10 +467,11 @@ class Engine final : public EngineBase {
     qcon_<<<g, kSliceThreads, qcon_smem_, s>>>(d_, Q_);
   }
   void launch_xstep(cudaStream_t s) {
-    k_xstep<T><<<S_, kSliceThreads, xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
+    xstep_<<<S_, kSliceThreads, xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
   }
   void launch_ystep(cudaStream_t s) {
-    dim3 g(S_, (n2_ + 31) / 32);
+    const int tw = 32 * ystep_cpl(rp_);
+    dim3 g(S_, (n2_ + tw - 1) / tw);
     ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
   }
 
@@ -516,6 +532,7 @@ class Engine final : public EngineBase {
   int slab_threads_ = 256;
   size_t slab_smem_ = 0, xstep_smem_ = 0, ystep_smem_ = 0, qcon_smem_ = 0;
   SlabFn<T> slab_[3] = {nullptr, nullptr, nullptr};
+  XFn<T> xstep_ = nullptr;
   YFn<T> ystep_ = nullptr;
   QFn<T> qcon_ = nullptr;
   cx<T>* Q_ = nullptr;

@@ -186,7 +186,8 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   YFn<T> ystep = pick_ystep<T>(rp);
   QFn<T> qcon = pick_qcon<T>(rp);
   for (int m = 0; m < 3; ++m) cudaFuncSetAttribute(slab[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
-  cudaFuncSetAttribute(k_xstep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xl.total);
+  XFn<T> xstep = pick_xstep<T>(rp);
+  cudaFuncSetAttribute(xstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xl.total);
   cudaFuncSetAttribute(ystep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm);
   cudaFuncSetAttribute(qcon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
   const int sis = slabs_in_smem ? 1 : 0;
@@ -207,8 +208,8 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   slab[MODE_ITER]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 1);
   for (int it = 0; it < n_iters; ++it) {
     qcon<<<dim3(S, (n1 + 31) / 32), kSliceThreads, qsm, st>>>(d, Q);
-    k_xstep<T><<<S, kSliceThreads, xl.total, st>>>(d, Q, xsmem ? 1 : 0);
-    ystep<<<dim3(S, (n2 + 31) / 32), kYThreads, ysm, st>>>(d);
+    xstep<<<S, kSliceThreads, xl.total, st>>>(d, Q, xsmem ? 1 : 0);
+    ystep<<<dim3(S, (n2 + 32 * ystep_cpl(rp) - 1) / (32 * ystep_cpl(rp))), kYThreads, ysm, st>>>(d);
     slab[MODE_ITER]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 0);
   }
   slab[MODE_W]<<<n1, 256, lay.total, st>>>(d, static_cast<T*>(W), sis, 0);
