@@ -30,32 +30,38 @@ __global__ void k_pack(const T* __restrict__ Gin, const uint8_t* __restrict__ Mi
 // real factor along mode 3, written to the half spectrum [S][r][n]:
 //   transposed = 0: input n x r x n3 (X0: i fastest, then s)
 //   transposed = 1: input r x n x n3 (Y0: s fastest, then i)
+// twg[m] = exp(-2 pi i m / n3); four interleaved partial sums.
 template <typename T>
-__global__ void k_factor_dft(const T* __restrict__ in, cx<T>* __restrict__ out, int n, int r, int n3, int transposed) {
+__global__ void k_factor_dft(const T* __restrict__ in, cx<T>* __restrict__ out, int n, int r, int n3, int transposed,
+                             const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
   const size_t total = (size_t)S * r * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n);
     const int s = (int)((e / n) % r);
     const int k = (int)(e / ((size_t)n * r));
-    double re = 0.0, im = 0.0;
+    cx<T> acc[4] = {};
+    int m = 0;  // k * l mod n3
     for (int l = 0; l < n3; ++l) {
       const size_t src = transposed ? ((size_t)s + (size_t)r * ((size_t)i + (size_t)n * l))
                                     : ((size_t)i + (size_t)n * ((size_t)s + (size_t)r * l));
-      const double v = (double)in[src];
-      double sn, cs;
-      sincospi(2.0 * (double)((long long)k * l % n3) / (double)n3, &sn, &cs);
-      re += v * cs;
-      im -= v * sn;
+      const T v = in[src];
+      const cx<T> w = twg[m];
+      acc[l & 3].re = fma(v, w.re, acc[l & 3].re);
+      acc[l & 3].im = fma(v, w.im, acc[l & 3].im);
+      m += k;
+      if (m >= n3) m -= n3;
     }
-    if (k == 0 || 2 * k == n3) im = 0.0;
-    out[e] = cx<T>{(T)re, (T)im};
+    cx<T> v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    if (k == 0 || 2 * k == n3) v.im = T(0);
+    out[e] = v;
   }
 }
 
 // Inverse of k_factor_dft (Eq. (barAAk)) back to the caller's layout.
 template <typename T>
-__global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out, int n, int r, int n3, int transposed) {
+__global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out, int n, int r, int n3, int transposed,
+                              const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
   const bool even = (n3 % 2) == 0;
   const int kmax = even ? S - 2 : S - 1;
@@ -71,19 +77,21 @@ __global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out,
       s = (int)((e / n) % r);
       l = (int)(e / ((size_t)n * r));
     }
-    double acc = (double)in[((size_t)0 * r + s) * n + i].re;
+    T acc[2] = {in[((size_t)0 * r + s) * n + i].re, T(0)};
+    int m = 0;  // k * l mod n3
     for (int k = 1; k <= kmax; ++k) {
+      m += l;
+      if (m >= n3) m -= n3;
       const cx<T> v = in[((size_t)k * r + s) * n + i];
-      double sn, cs;
-      sincospi(2.0 * (double)((long long)k * l % n3) / (double)n3, &sn, &cs);
-      // 2 Re(v * exp(+i theta))
-      acc += 2.0 * ((double)v.re * cs - (double)v.im * sn);
+      const cx<T> w = twg[m];
+      // 2 Re(v exp(+i 2 pi k l / n3)) = 2 (v.re w.re + v.im w.im)
+      acc[k & 1] = fma(T(2) * v.re, w.re, fma(T(2) * v.im, w.im, acc[k & 1]));
     }
     if (even) {
-      const double nyq = (double)in[((size_t)(S - 1) * r + s) * n + i].re;
-      acc += (l & 1) ? -nyq : nyq;
+      const T nyq = in[((size_t)(S - 1) * r + s) * n + i].re;
+      acc[0] += (l & 1) ? -nyq : nyq;
     }
-    out[e] = (T)(acc / (double)n3);
+    out[e] = (acc[0] + acc[1]) / T(n3);
   }
 }
 
@@ -125,10 +133,6 @@ __global__ void k_rho1_term(Dev<T> d) {
     d.part_k[k] = s;
   }
 }
-
-}  // namespace tc
-
-namespace tc {
 
 // Initial Z~ = X~Y~ (step 3 at the initial point; during the iteration the
 // Y-step kernel writes Z~).  One thread per output.

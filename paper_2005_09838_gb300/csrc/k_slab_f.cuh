@@ -31,9 +31,10 @@ namespace tc {
 
 constexpr int kSlabFThreads = 512;
 
-// Floats between consecutive tubes: odd, and room for the M + 1 complex values
-// of the half spectrum.
-__host__ __device__ constexpr int slab_f_stride(int L) { return (L + 2) | 1; }
+// Floats between consecutive tubes: room for the M + 1 complex values of the
+// half spectrum, even (complex slots are 8-byte aligned) with an odd number of
+// complex values (a warp's slot accesses across 32 tubes hit distinct banks).
+__host__ __device__ constexpr int slab_f_stride(int L) { return (((L + 2) / 2) % 2 == 1) ? L + 2 : L + 4; }
 
 struct SlabFLayout {
   size_t msk, stw, wtab, red, buf, total;  // byte offsets and total shared bytes
@@ -68,13 +69,26 @@ __device__ __forceinline__ int slab_f_off(int l) {
 
 template <typename T>
 __device__ __forceinline__ cx<T> ld_slot(const T* tb, int slot) {
-  return cx<T>{tb[2 * slot], tb[2 * slot + 1]};
+  return reinterpret_cast<const cx<T>*>(tb)[slot];
 }
 template <typename T>
 __device__ __forceinline__ void st_slot(T* tb, int slot, cx<T> v) {
-  tb[2 * slot] = v.re;
-  tb[2 * slot + 1] = v.im;
+  reinterpret_cast<cx<T>*>(tb)[slot] = v;
 }
+
+// (group, tube) items of a pass, tube index fastest, strided by the block size
+// (replaces a division per item).
+struct ItemIter {
+  int g, t;
+  __device__ __forceinline__ ItemIter(int e, int n2) : g(e / n2), t(e - (e / n2) * n2) {}
+  __device__ __forceinline__ void advance(int nt, int n2) {
+    t += nt;
+    while (t >= n2) {
+      t -= n2;
+      ++g;
+    }
+  }
+};
 
 // One entry of the packed sequence for the inverse real transform:
 // z_k = E + i O, E = (a + conj b)/2, O = (a - conj b)/2 * w_L^{-k}, with
@@ -135,54 +149,51 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
     // the half spectrum lands in slots 0..M of every tube through asynchronous
     // copies (all in flight at once), then is split in place
     const cx<T>* src = (MODE == MODE_ITER) ? zrow : rrow;
-    int k = tid / n2, t = tid - (tid / n2) * n2;
-    for (int e = tid; e < (M + 1) * n2; e += nt) {
-      const T* g = reinterpret_cast<const T*>(src + e);
-      T* dst = buf + (size_t)t * LP + 2 * k;
-      cp_async_elem(dst, g);
-      cp_async_elem(dst + 1, g + 1);
-      t += nt;
-      while (t >= n2) {
-        t -= n2;
-        ++k;
-      }
-    }
+    ItemIter it(tid, n2);
+    for (int e = tid; e < (M + 1) * n2; e += nt, it.advance(nt, n2))
+      cp_async_elem(reinterpret_cast<cx<T>*>(buf + (size_t)it.t * LP) + it.g, src + e);
     cp_async_wait_all();
     __syncthreads();
   }
-  for (int e = tid; e < (M / 2 + 1) * n2; e += nt) {
-    const int k = e / n2, t = e - k * n2;
-    const int kc = M - k;
-    T* tb = buf + (size_t)t * LP;
-    cx<T> a, b;
-    if (MODE == MODE_W) {
-      a = ldg_cx(zrow + (size_t)k * n2 + t) + ldg_cx(rrow + (size_t)k * n2 + t);
-      b = ldg_cx(zrow + (size_t)kc * n2 + t) + ldg_cx(rrow + (size_t)kc * n2 + t);
-    } else {
-      a = ld_slot(tb, k);
-      b = ld_slot(tb, kc);
+  {
+    ItemIter it(tid, n2);
+    for (int e = tid; e < (M / 2 + 1) * n2; e += nt, it.advance(nt, n2)) {
+      const int k = it.g, t = it.t;
+      const int kc = M - k;
+      T* tb = buf + (size_t)t * LP;
+      cx<T> a, b;
+      if (MODE == MODE_W) {
+        a = ldg_cx(zrow + (size_t)k * n2 + t) + ldg_cx(rrow + (size_t)k * n2 + t);
+        b = ldg_cx(zrow + (size_t)kc * n2 + t) + ldg_cx(rrow + (size_t)kc * n2 + t);
+      } else {
+        a = ld_slot(tb, k);
+        b = ld_slot(tb, kc);
+      }
+      if (k == 0) {  // DC and Nyquist slices are real
+        a.im = T(0);
+        b.im = T(0);
+      }
+      st_slot(tb, k, inv_split<T, L>(a, b, k));
+      if (k != 0 && k != kc) st_slot(tb, kc, inv_split<T, L>(b, a, kc));
     }
-    if (k == 0) {  // DC and Nyquist slices are real
-      a.im = T(0);
-      b.im = T(0);
-    }
-    st_slot(tb, k, inv_split<T, L>(a, b, k));
-    if (k != 0 && k != kc) st_slot(tb, kc, inv_split<T, L>(b, a, kc));
   }
   __syncthreads();
 
   // ---- A2: inverse DFT_N1 over slots N2 n1 + q, twiddle w_M^{-q k1} ------------------------
-  for (int e = tid; e < N2 * n2; e += nt) {
-    const int q = e / n2, t = e - q * n2;
-    T* tb = buf + (size_t)t * LP;
-    cx<T> v[N1], o[N1];
+  {
+    ItemIter it(tid, n2);
+    for (int e = tid; e < N2 * n2; e += nt, it.advance(nt, n2)) {
+      const int q = it.g;
+      T* tb = buf + (size_t)it.t * LP;
+      cx<T> v[N1], o[N1];
 #pragma unroll
-    for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
-    fft::CFFT<T, N1, L, true>::run(v, 1, o);
+      for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
+      fft::CFFT<T, N1, L, true>::run(v, 1, o);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      const cx<T> x = (k1 == 0) ? o[0] : cmul(o[k1], fft::tw<T, L, true>(2 * q * k1));
-      st_slot(tb, N2 * k1 + q, x);
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const cx<T> x = (k1 == 0) ? o[0] : cmul(o[k1], fft::tw<T, L, true>(2 * q * k1));
+        st_slot(tb, N2 * k1 + q, x);
+      }
     }
   }
   __syncthreads();
@@ -190,41 +201,43 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   // ---- A3: inverse DFT_N2 over slots N2 k1 + j -> spatial values; v = G on the mask -------
   // (the G values of the next item are loaded while the current one is computed)
   const T scale = T(1) / T(M);
-  T gn[2 * N2];
-  auto load_g = [&](int e) {
-    const int k1 = e / n2, t = e - k1 * n2;
+  {
+    T gn[2 * N2];
+    auto load_g = [&](int k1, int t) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      const int l = 2 * (k1 + N1 * k2);
-      gn[2 * k2] = __ldg(Gi + (size_t)l * n2 + t);
-      gn[2 * k2 + 1] = __ldg(Gi + (size_t)(l + 1) * n2 + t);
-    }
-  };
-  if (MODE == MODE_ITER && tid < N1 * n2) load_g(tid);
-  for (int e = tid; e < N1 * n2; e += nt) {
-    const int k1 = e / n2, t = e - k1 * n2;
-    T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
-    T g[2 * N2];
-    if (MODE == MODE_ITER) {
-#pragma unroll
-      for (int q = 0; q < 2 * N2; ++q) g[q] = gn[q];
-      if (e + nt < N1 * n2) load_g(e + nt);
-    }
-    cx<T> v[N2], o[N2];
-#pragma unroll
-    for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
-    fft::CFFT<T, N2, L, true>::run(v, 1, o);
-#pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      T x0 = o[k2].re * scale, x1 = o[k2].im * scale;
-      if (MODE == MODE_ITER) {
+      for (int k2 = 0; k2 < N2; ++k2) {
         const int l = 2 * (k1 + N1 * k2);
-        const uint32_t w0 = msk[l * mw + (t >> 5)], w1 = msk[(l + 1) * mw + (t >> 5)];
-        x0 = ((w0 >> (t & 31)) & 1u) ? g[2 * k2] : x0 * zfac;
-        x1 = ((w1 >> (t & 31)) & 1u) ? g[2 * k2 + 1] : x1 * zfac;
+        gn[2 * k2] = __ldg(Gi + (size_t)l * n2 + t);
+        gn[2 * k2 + 1] = __ldg(Gi + (size_t)(l + 1) * n2 + t);
       }
-      tb[2 * k2] = x0;
-      tb[2 * k2 + 1] = x1;
+    };
+    ItemIter it(tid, n2);
+    if (MODE == MODE_ITER && tid < N1 * n2) load_g(it.g, it.t);
+    for (int e = tid; e < N1 * n2; e += nt) {
+      const int k1 = it.g, t = it.t;
+      it.advance(nt, n2);
+      T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
+      T g[2 * N2];
+      if (MODE == MODE_ITER) {
+#pragma unroll
+        for (int q = 0; q < 2 * N2; ++q) g[q] = gn[q];
+        if (e + nt < N1 * n2) load_g(it.g, it.t);
+      }
+      cx<T> v[N2], o[N2];
+#pragma unroll
+      for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
+      fft::CFFT<T, N2, L, true>::run(v, 1, o);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        T x0 = o[k2].re * scale, x1 = o[k2].im * scale;
+        if (MODE == MODE_ITER) {
+          const int l = 2 * (k1 + N1 * k2);
+          const uint32_t w0 = msk[l * mw + (t >> 5)], w1 = msk[(l + 1) * mw + (t >> 5)];
+          x0 = ((w0 >> (t & 31)) & 1u) ? g[2 * k2] : x0 * zfac;
+          x1 = ((w1 >> (t & 31)) & 1u) ? g[2 * k2 + 1] : x1 * zfac;
+        }
+        st_slot(tb, k2, cx<T>{x0, x1});
+      }
     }
   }
   __syncthreads();
@@ -264,50 +277,59 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   }
 
   // ---- C1: forward DFT_N2 over slots N2 k1 + j, twiddle w_M^{k1 q} -----------------------
-  for (int e = tid; e < N1 * n2; e += nt) {
-    const int k1 = e / n2, t = e - k1 * n2;
-    T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
-    cx<T> v[N2], o[N2];
+  {
+    ItemIter it(tid, n2);
+    for (int e = tid; e < N1 * n2; e += nt, it.advance(nt, n2)) {
+      const int k1 = it.g;
+      T* tb = buf + (size_t)it.t * LP + 2 * N2 * k1;
+      cx<T> v[N2], o[N2];
 #pragma unroll
-    for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
-    fft::CFFT<T, N2, L, false>::run(v, 1, o);
+      for (int j = 0; j < N2; ++j) v[j] = ld_slot(tb, j);
+      fft::CFFT<T, N2, L, false>::run(v, 1, o);
 #pragma unroll
-    for (int q = 0; q < N2; ++q) {
-      const cx<T> x = (q == 0) ? o[0] : cmul(o[q], fft::tw<T, L, false>(2 * k1 * q));
-      st_slot(tb, q, x);
+      for (int q = 0; q < N2; ++q) {
+        const cx<T> x = (q == 0) ? o[0] : cmul(o[q], fft::tw<T, L, false>(2 * k1 * q));
+        st_slot(tb, q, x);
+      }
     }
   }
   __syncthreads();
 
   // ---- C2: forward DFT_N1 over slots N2 k1 + q -> natural order -----------------------------
-  for (int e = tid; e < N2 * n2; e += nt) {
-    const int q = e / n2, t = e - q * n2;
-    T* tb = buf + (size_t)t * LP;
-    cx<T> v[N1], o[N1];
+  {
+    ItemIter it(tid, n2);
+    for (int e = tid; e < N2 * n2; e += nt, it.advance(nt, n2)) {
+      const int q = it.g;
+      T* tb = buf + (size_t)it.t * LP;
+      cx<T> v[N1], o[N1];
 #pragma unroll
-    for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
-    fft::CFFT<T, N1, L, false>::run(v, 1, o);
+      for (int j = 0; j < N1; ++j) v[j] = ld_slot(tb, N2 * j + q);
+      fft::CFFT<T, N1, L, false>::run(v, 1, o);
 #pragma unroll
-    for (int j = 0; j < N1; ++j) st_slot(tb, N2 * j + q, o[j]);
+      for (int j = 0; j < N1; ++j) st_slot(tb, N2 * j + q, o[j]);
+    }
   }
   __syncthreads();
 
   // ---- C3: split to the half spectrum; R~ = W~ - Z~ ------------------------------------------
   cx<T>* rt = d.Rt + (size_t)i1 * (M + 1) * n2;
-  for (int e = tid; e < (M / 2 + 1) * n2; e += nt) {
-    const int k = e / n2, t = e - k * n2;
-    const int kc = M - k;
-    const T* tb = buf + (size_t)t * LP;
-    const size_t ok = (size_t)k * n2 + t, oc = (size_t)kc * n2 + t;
-    const cx<T> zk0 = ldg_cx(zrow + ok), zc0 = ldg_cx(zrow + oc);
-    if (k == 0) {
-      const cx<T> z0 = ld_slot(tb, 0);
-      rt[ok] = cx<T>{z0.re + z0.im, T(0)} - cx<T>{zk0.re, T(0)};
-      rt[oc] = cx<T>{z0.re - z0.im, T(0)} - cx<T>{zc0.re, T(0)};
-    } else {
-      const cx<T> zk = ld_slot(tb, k), zm = ld_slot(tb, kc);
-      rt[ok] = fwd_split<T, L>(zk, zm, k) - zk0;
-      if (k != kc) rt[oc] = fwd_split<T, L>(zm, zk, kc) - zc0;
+  {
+    ItemIter it(tid, n2);
+    for (int e = tid; e < (M / 2 + 1) * n2; e += nt, it.advance(nt, n2)) {
+      const int k = it.g, t = it.t;
+      const int kc = M - k;
+      const T* tb = buf + (size_t)t * LP;
+      const size_t ok = (size_t)k * n2 + t, oc = (size_t)kc * n2 + t;
+      const cx<T> zk0 = ldg_cx(zrow + ok), zc0 = ldg_cx(zrow + oc);
+      if (k == 0) {
+        const cx<T> z0 = ld_slot(tb, 0);
+        rt[ok] = cx<T>{z0.re + z0.im - zk0.re, T(0)};
+        rt[oc] = cx<T>{z0.re - z0.im - zc0.re, T(0)};
+      } else {
+        const cx<T> zk = ld_slot(tb, k), zm = ld_slot(tb, kc);
+        rt[ok] = fwd_split<T, L>(zk, zm, k) - zk0;
+        if (k != kc) rt[oc] = fwd_split<T, L>(zm, zk, kc) - zc0;
+      }
     }
   }
 }

@@ -93,15 +93,18 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 constexpr int kMaxRank = 32;
 
-// Asynchronous 4- or 8-byte global -> shared copy (cp.async, L1-allocating).
+// Asynchronous 4-, 8- or 16-byte global -> shared copy (cp.async, L1-allocating);
+// both addresses aligned to the element size.
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element size");
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async element size");
   const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
   if constexpr (sizeof(T) == 4)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(gsrc) : "memory");
-  else
+  else if constexpr (sizeof(T) == 8)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gsrc) : "memory");
 }
 
 // Wait for every cp.async of this thread (the block still needs a barrier).

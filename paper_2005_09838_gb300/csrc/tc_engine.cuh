@@ -290,9 +290,9 @@ class Engine final : public EngineBase {
     }
     k_pack<T><<<n1_ * n3_, 256, 0, stream_>>>(dG, dM, Gint, maskbits, n1_, n2_, n3_, mw_);
     const int fgrid = 4 * 152;
-    k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dY, Yt, n2_, r_, n3_, 1);
+    k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dY, Yt, n2_, r_, n3_, 1, twg);
     if (dX) {
-      k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dX, Xt, n1_, r_, n3_, 0);
+      k_factor_dft<T><<<fgrid, 256, 0, stream_>>>(dX, Xt, n1_, r_, n3_, 0, twg);
     } else {
       cudaMemsetAsync(Xt, 0, nx * sizeof(cx<T>), stream_);
     }
@@ -388,8 +388,8 @@ class Engine final : public EngineBase {
     }
     if (dW) launch_slab(MODE_W, dW, 0, stream_);
     const int fgrid = 4 * 152;
-    if (dXo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Xt, dXo, n1_, r_, n3_, 0);
-    if (dYo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Yt, dYo, n2_, r_, n3_, 1);
+    if (dXo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Xt, dXo, n1_, r_, n3_, 0, d_.twg);
+    if (dYo) k_factor_idft<T><<<fgrid, 256, 0, stream_>>>(d_.Yt, dYo, n2_, r_, n3_, 1, d_.twg);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !on_device) {
       if (W) e = cudaMemcpyAsync(W, dW, N * sizeof(T), cudaMemcpyDeviceToHost, stream_);

@@ -197,9 +197,9 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   cudaMemsetAsync(d.err, 0, sizeof(int), st);
   k_static_tables<T><<<3, 256, 0, st>>>(winv, hinv, twg, n1, n2, n3, p.mu, p.rho1, p.rho2);
   k_pack<T><<<n1 * n3, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, mw);
-  k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(Y0), d.Yt, n2, r, n3, 1);
+  k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(Y0), d.Yt, n2, r, n3, 1, twg);
   if (X0) {
-    k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(X0), d.Xt, n1, r, n3, 0);
+    k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(X0), d.Xt, n1, r, n3, 0, twg);
   } else {
     cudaMemsetAsync(d.Xt, 0, nx * sizeof(cx<T>), st);
   }
