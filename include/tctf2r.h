@@ -51,7 +51,9 @@ typedef enum { TC_FP64 = 0, TC_FP32 = 1, TC_TF32 = 2, TC_BF16 = 3 } tc_precision
 /* Step rule of Eq. (updataXYW1).  TC_STEP_EXACT takes alpha_kl = L_k1 and
  * beta_kl = L_k2 (unit steps along d_X, d_Y: exact minimisation of the
  * quadratic h_k in each block).  TC_STEP_SCALED uses the fixed alpha, beta
- * below divided by L_k1 = ||H_rho1||_2 ||Y~Y~^*||_2 and L_k2 = ||X~^* H_rho1 X~||_2. */
+ * below divided by L_k1 = ||H_rho1||_2 ||Y~Y~^*||_2 and L_k2 = ||X~^* H_rho1 X~||_2
+ * (no line search); the Gram matrices then go through the eigendecomposition,
+ * which gives the 2-norms. */
 typedef enum { TC_STEP_EXACT = 0, TC_STEP_SCALED = 1 } tc_step;
 
 /* Problem statement of the TCTF2R Algorithm (Sec. 4.1, "Input").  H and K are
@@ -96,10 +98,13 @@ tc_status tc_init(tc_ctx** out, const tc_params* p, const void* G, const uint8_t
 
 /* Run n_iters iterations of the TCTF2R Algorithm (steps 1-4 and 7 of Sec. 4.1;
  * step 5 keeps r fixed).  Asynchronous: work is enqueued on the context's
- * stream and the call returns without waiting, unless p->eps > 0, in which case
- * the stopping test of step 6 is evaluated after every iteration (with a device
- * synchronisation) and the loop ends early when it holds.
- *   done : receives the number of iterations run (may be NULL)
+ * stream and the call returns without waiting.  With p->eps > 0 the stopping
+ * test of step 6 (||X~' - X~||_inf <= eps, ||Y~' - Y~||_inf <= eps and
+ * ||W' - W||_F <= eps, ||.||_inf the largest modulus of an entry) is evaluated
+ * on the device after every iteration; once it holds, the remaining launched
+ * iterations do no work and the state stays at the iterate that passed it.
+ *   done : receives the number of iterations run in this call (may be NULL;
+ *          when given and p->eps > 0 the call synchronises the stream)
  * Errors: TC_ERR_ARG (n_iters < 0), TC_ERR_CUDA, TC_ERR_STATE. */
 tc_status tc_iterate(tc_ctx* c, int32_t n_iters, int32_t* done);
 
@@ -117,7 +122,7 @@ tc_status tc_objective(tc_ctx* c, double* f0, double* resid_obs);
 tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device);
 
 /* Profiling aid: run n_iters real iterations (they advance the state exactly
- * like tc_iterate) but launch the three per-iteration kernels one by one, with
+ * like tc_iterate) but launch the four per-iteration kernels one by one, with
  * CUDA events recorded around each on the context's stream, then synchronise.
  *   ms : receives 4 values, the mean device time per launch in milliseconds of
  *        the four kernels of one iteration, in launch order: the X-step
@@ -126,6 +131,17 @@ tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device)
  *        forward DFT).
  * Errors: TC_ERR_ARG (n_iters < 1 or ms NULL), TC_ERR_CUDA, TC_ERR_STATE. */
 tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
+
+/* State of the stopping test of step 6 (contexts created with p->eps > 0).
+ * Synchronises the stream.
+ *   changes   : receives 3 values of the last iteration run: ||X~' - X~||_inf,
+ *               ||Y~' - Y~||_inf (largest modulus over the half spectrum, equal
+ *               to that over all slices) and ||W' - W||_F (spatial)
+ *   stopped   : receives 1 once the test has held, else 0 (may be NULL)
+ *   iters_run : receives the iterations run since tc_init (may be NULL)
+ * Errors: TC_ERR_ARG (changes NULL), TC_ERR_STATE (eps = 0 or poisoned),
+ * TC_ERR_CUDA. */
+tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* iters_run);
 
 /* Allocation-free completion of a small tensor (this entry point has no
  * counterpart in the paper; it is a deployment aid).  Some callers cannot call

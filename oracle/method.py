@@ -342,18 +342,20 @@ def w_step_kkt(Z, G, mask, mu, rho2):
 
 def tctf2r(G, mask, r, mu, rho1, rho2, Y0, X0=None, iters=10, step="exact",
            alpha=1.0, beta=1.0, rtol=None, half=True, sign=+1,
-           wstep="kkt", record=False):
+           wstep="kkt", record=False, eps=0.0):
     """Run ``iters`` iterations of the TCTF2R Algorithm.
 
     Steps per iteration l (Sec. 4.1): 1. X-update of every slice with Y, W
     fixed; 2. Y-update of every slice with the new X; 3. Z~ = X~ Y~ and Z by
     Eq. (barAAk); 4. W-update (Eq. (subquKKT)); 7. W~ by Eq. (bar BA-k).
     With ``half`` only floor(m3/2)+1 slices are solved and the rest mirrored
-    (remark after the algorithm).  Step 5 keeps r fixed; step 6 (stopping
-    test) is recorded, not applied: the loop runs exactly ``iters`` times.
+    (remark after the algorithm).  Step 5 keeps r fixed.  Step 6: with
+    ``eps`` > 0 the loop ends after the first iteration with
+    ||X~' - X~||_inf <= eps, ||Y~' - Y~||_inf <= eps and ||W' - W||_F <= eps
+    (||.||_inf: largest modulus of an entry), else it runs ``iters`` times.
 
-    Returns a dict with W, Z, X, Y (spatial), Xt, Yt (all slices), f0 and,
-    with ``record``, per-iteration histories.
+    Returns a dict with W, Z, X, Y (spatial), Xt, Yt (all slices), f0, the
+    number of iterations run and, with ``record``, per-iteration histories.
     """
     G = np.asarray(G, dtype=np.float64)
     mask = np.asarray(mask, dtype=bool)
@@ -365,6 +367,7 @@ def tctf2r(G, mask, r, mu, rho1, rho2, Y0, X0=None, iters=10, step="exact",
     Xt = dft3(X0, sign=sign)
     Yt = dft3(np.asarray(Y0, np.float64), sign=sign)
     hist = {"f0": [], "f0_after_x": [], "f0_after_y": [], "dX": [], "dY": [], "dW": []}
+    run = 0
     for _ in range(iters):
         Xold, Yold, Wold = Xt.copy(), Yt.copy(), W.copy()
         Xn = np.zeros_like(Xt)
@@ -390,17 +393,62 @@ def tctf2r(G, mask, r, mu, rho1, rho2, Y0, X0=None, iters=10, step="exact",
         else:
             W = w_step_kkt(Z, G, mask, mu, rho2)
         Wt = dft3(W, sign=sign)
+        run += 1
+        dX = float(np.max(np.abs(Xt - Xold)))
+        dY = float(np.max(np.abs(Yt - Yold)))
+        dW = float(np.linalg.norm(W - Wold))
         if record:
             hist["f0"].append(objective_freq(Xt, Yt, Wt, mu, rho1, rho2))
-            hist["dX"].append(float(np.max(np.abs(Xt - Xold))))
-            hist["dY"].append(float(np.max(np.abs(Yt - Yold))))
-            hist["dW"].append(float(np.linalg.norm(W - Wold)))
+            hist["dX"].append(dX)
+            hist["dY"].append(dY)
+            hist["dW"].append(dW)
+        if eps > 0 and dX <= eps and dY <= eps and dW <= eps:
+            break
     X = idft3(Xt, sign=sign).real
     Y = idft3(Yt, sign=sign).real
     Z = tprod(X, Y, sign=sign)
     out = {"W": W, "Z": Z, "X": X, "Y": Y, "Xt": Xt, "Yt": Yt, "Wt": Wt,
            "f0": objective(X, Y, W, mu, rho1, rho2, sign=sign)}
     out["resid_obs"] = float(np.sqrt(np.sum(((Z - G) * mask) ** 2)))
+    out["iters"] = run
     if record:
         out["hist"] = hist
     return out
+
+
+# ---------------------------------------------------------------------------
+# Differentiation form: the factor terms of f0 as a loss of (X, Y)
+# ---------------------------------------------------------------------------
+
+def ttranspose(A: np.ndarray) -> np.ndarray:
+    """Conjugate transpose A^* of a real third-order tensor (Sec. 2, after
+    Definition "T-ProdDef"): every frontal slice transposed, the order of
+    frontal slices 2..m3 reversed."""
+    At = np.transpose(np.asarray(A), (1, 0, 2))
+    return np.concatenate([At[:, :, :1], At[:, :, :0:-1]], axis=2)
+
+
+def factor_loss(X, Y, G, mask, rho1) -> float:
+    """L(X, Y) = 1/2 ||P_Omega(X*Y - G)||_F^2 + rho1/2 ||H unfold(X*Y, 1)||_F^2:
+    the terms of f0 (Eq. (TETP-optim)) that involve the factors, with W held at
+    G on the mask."""
+    Z = tprod(X, Y)
+    m1 = Z.shape[0]
+    R = np.where(mask, Z - G, 0.0)
+    f = 0.5 * np.sum(R ** 2)
+    if m1 > 1:
+        f += 0.5 * rho1 * np.sum((toeplitz_D(m1) @ unfold(Z, 1)) ** 2)
+    return float(f)
+
+
+def factor_loss_grad(X, Y, G, mask, rho1):
+    """Gradients of factor_loss.  With E = P_Omega(X*Y - G) + rho1 (H^T H) x_1
+    (X*Y), the gradient with respect to Z = X*Y, they are dL/dX = E * Y^* and
+    dL/dY = X^* * E (t-products with the conjugate transpose)."""
+    Z = tprod(X, Y)
+    m1 = Z.shape[0]
+    E = np.where(mask, Z - G, 0.0)
+    if m1 > 1:
+        D = toeplitz_D(m1)
+        E = E + rho1 * np.einsum("ab,bjk->ajk", D.T @ D, Z)
+    return tprod(E, ttranspose(Y)), tprod(ttranspose(X), E)

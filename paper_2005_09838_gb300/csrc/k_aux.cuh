@@ -95,6 +95,32 @@ __global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out,
   }
 }
 
+// Stopping test of the Algorithm (step 6), one warp after each iteration:
+// stop once ||X~^{l+1} - X~^l||_inf <= eps, ||Y~^{l+1} - Y~^l||_inf <= eps and
+// ||W^{l+1} - W^l||_F <= eps.  ||.||_inf is the largest modulus of an entry;
+// ||dW||_F comes from the half spectrum by Parseval (sum over all n3 slices of
+// |dW~_k|^2 divided by n3).  Counts the iterations run and resets the maxima.
+template <typename T>
+__global__ void k_check(Dev<T> d) {
+  unsigned long long* c = d.conv;
+  if (c[2] != 0ull) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < d.n1; i += 32) s += d.part_dw[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) {
+    const double dx = __longlong_as_double((long long)c[0]);
+    const double dy = __longlong_as_double((long long)c[1]);
+    const double dw = sqrt(s / (double)d.n3);
+    c[3] += 1ull;
+    c[4] = (unsigned long long)__double_as_longlong(dx);
+    c[5] = (unsigned long long)__double_as_longlong(dy);
+    c[6] = (unsigned long long)__double_as_longlong(dw);
+    if (dx <= d.eps && dy <= d.eps && dw <= d.eps) c[2] = 1ull;
+    c[0] = 0ull;
+    c[1] = 0ull;
+  }
+}
+
 // rho1 term of f0 per slice: tr((X~^H H^T H X~)(Y~ Y~^H)) in FP64.
 template <typename T>
 __global__ void k_rho1_term(Dev<T> d) {

@@ -198,6 +198,16 @@ __device__ void wstep_sweeps(T* __restrict__ col, int LP, const uint32_t* __rest
     wstep_bwd_word<T, true, false>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
 }
 
+// Weighted |W~^{l+1} - W~^l|^2 of one half-spectrum entry: W~ = Z~ + R~, so the
+// change is (R~new - R~old) + (Z~new - Z~old); weight 1 for the real slices
+// (k = 0 and, for even n3, k = n3/2), 2 for the others (their mirror).
+template <typename T>
+__device__ __forceinline__ double dw_term(cx<T> rnew, cx<T> rold, cx<T> dz, int k, int n3) {
+  const double a = (double)rnew.re - (double)rold.re + (double)dz.re;
+  const double b = (double)rnew.im - (double)rold.im + (double)dz.im;
+  return ((k == 0 || 2 * k == n3) ? 1.0 : 2.0) * (a * a + b * b);
+}
+
 // ---------------------------------------------------------------------------
 // Generic (any n3) direct transforms of one tube: the sums of Eq. (bar BA-k)
 // and Eq. (barAAk).
@@ -220,10 +230,12 @@ __device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int n3, c
   }
 }
 
-// Forward transform of a tube minus the spectrum zsub (R~ = W~ - Z~).
+// Forward transform of a tube minus the spectrum zsub (R~ = W~ - Z~).  With
+// dz (Z~^{l+1} - Z~^l) non-null, dw2 accumulates the weighted |W~^{l+1} -
+// W~^l|^2 of the half spectrum (weight 2 for slices with a conjugate partner).
 template <typename T>
 __device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, cx<T>* out, size_t stride, int n3,
-                                 const cx<T>* __restrict__ twg) {
+                                 const cx<T>* __restrict__ twg, const cx<T>* __restrict__ dz, double& dw2) {
   const int S = n3 / 2 + 1;
   for (int k = 0; k < S; ++k) {
     cx<T> acc = {T(0), T(0)};
@@ -234,7 +246,9 @@ __device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, 
       acc.im += x * w.im;
     }
     if (k == 0 || (2 * k == n3)) acc.im = T(0);
-    out[k * stride] = acc - zsub[k * stride];
+    const cx<T> rn = acc - zsub[k * stride];
+    if (dz) dw2 += dw_term(rn, out[k * stride], dz[k * stride], k, n3);
+    out[k * stride] = rn;
   }
 }
 
@@ -257,6 +271,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   const int S = n3 / 2 + 1;
   const int LP = slab_stride(n3);
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (MODE == MODE_ITER && !init && converged(d)) return;
   if (L > 0 && d.n3 != L) {
     if (tid == 0) set_err(d.err, DEV_BAD_LAUNCH);
     return;
@@ -399,6 +414,8 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   }
 
   // ---- phase C: forward transform, R~ = W~ - Z~ ------------------------------
+  const bool track = !init && d.dZt != nullptr;
+  double dw2 = 0.0;
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
     for (int t = tid; t < n2; t += nt) {
@@ -410,12 +427,23 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       cx<T>* rt = d.Rt + (size_t)i1 * SL * n2 + t;
       const cx<T>* zt = zrow + t;
 #pragma unroll
-      for (int k = 0; k < SL; ++k) rt[(size_t)k * n2] = X[k] - ldg_cx(zt + (size_t)k * n2);
+      for (int k = 0; k < SL; ++k) {
+        const cx<T> rn = X[k] - ldg_cx(zt + (size_t)k * n2);
+        if (track) dw2 += dw_term(rn, rt[(size_t)k * n2], d.dZt[(size_t)i1 * SL * n2 + (size_t)k * n2 + t], k, L);
+        rt[(size_t)k * n2] = rn;
+      }
     }
   } else {
     for (int t = tid; t < n2; t += nt) {
-      generic_rdft_sub<T>(spat + (size_t)t * LP, zrow + t, d.Rt + (size_t)i1 * S * n2 + t, (size_t)n2, n3, d.twg);
+      const size_t o = (size_t)i1 * S * n2 + t;
+      generic_rdft_sub<T>(spat + (size_t)t * LP, zrow + t, d.Rt + o, (size_t)n2, n3, d.twg,
+                          track ? d.dZt + o : nullptr, dw2);
     }
+  }
+  if (track) {
+    double unused = 0.0;
+    block_sum2(dw2, unused, red);
+    if (tid == 0) d.part_dw[i1] = dw2;
   }
 }
 

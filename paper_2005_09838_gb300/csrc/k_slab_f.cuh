@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   const int i1 = blockIdx.x;
   const int n1 = d.n1, n2 = d.n2, mw = d.mw;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (MODE == MODE_ITER && !init && converged(d)) return;
   if (d.n3 != L) {
     if (tid == 0) set_err(d.err, DEV_BAD_LAUNCH);
     return;
@@ -313,6 +314,9 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
 
   // ---- C3: split to the half spectrum; R~ = W~ - Z~ ------------------------------------------
   cx<T>* rt = d.Rt + (size_t)i1 * (M + 1) * n2;
+  const bool track = !init && d.dZt != nullptr;
+  const cx<T>* dz = track ? d.dZt + (size_t)i1 * (M + 1) * n2 : nullptr;
+  double dw2 = 0.0;
   {
     ItemIter it(tid, n2);
     for (int e = tid; e < (M / 2 + 1) * n2; e += nt, it.advance(nt, n2)) {
@@ -321,16 +325,28 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
       const T* tb = buf + (size_t)t * LP;
       const size_t ok = (size_t)k * n2 + t, oc = (size_t)kc * n2 + t;
       const cx<T> zk0 = ldg_cx(zrow + ok), zc0 = ldg_cx(zrow + oc);
+      cx<T> rk, rc;
       if (k == 0) {
         const cx<T> z0 = ld_slot(tb, 0);
-        rt[ok] = cx<T>{z0.re + z0.im - zk0.re, T(0)};
-        rt[oc] = cx<T>{z0.re - z0.im - zc0.re, T(0)};
+        rk = cx<T>{z0.re + z0.im - zk0.re, T(0)};
+        rc = cx<T>{z0.re - z0.im - zc0.re, T(0)};
       } else {
         const cx<T> zk = ld_slot(tb, k), zm = ld_slot(tb, kc);
-        rt[ok] = fwd_split<T, L>(zk, zm, k) - zk0;
-        if (k != kc) rt[oc] = fwd_split<T, L>(zm, zk, kc) - zc0;
+        rk = fwd_split<T, L>(zk, zm, k) - zk0;
+        rc = fwd_split<T, L>(zm, zk, kc) - zc0;
       }
+      if (track) {
+        dw2 += dw_term(rk, rt[ok], dz[ok], k, L);
+        if (k != kc) dw2 += dw_term(rc, rt[oc], dz[oc], kc, L);
+      }
+      rt[ok] = rk;
+      if (k != kc) rt[oc] = rc;
     }
+  }
+  if (track) {
+    double unused = 0.0;
+    block_sum2(dw2, unused, red);
+    if (tid == 0) d.part_dw[i1] = dw2;
   }
 }
 

@@ -28,7 +28,7 @@ namespace tc {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
-                                        T rtol);
+                                        T rtol, T* lmax_out);
 
 template <typename T>
 __device__ inline T warp_norm1_bound(const cx<T>* M, int ld, int col0, int r) {
@@ -145,9 +145,15 @@ __device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in)
 
 template <typename T, int RP>
 __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
-                                      int r, T rtol) {
+                                      int r, T rtol, bool force_eig = false) {
   const int tid = threadIdx.x, nt = blockDim.x;
   int ok;
+  if (force_eig) {
+    // the eigendecomposition is wanted for lambda_max (scaled steps): sred[2]
+    if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
+    __syncthreads();
+    return 0;
+  }
   if constexpr (RP <= 16) {
     // W receives A^-1 (row-major r x r)
     if (tid < 32) {
@@ -202,7 +208,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
     }
   }
   __syncthreads();
-  if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol);
+  if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
   __syncthreads();
   return 0;
 }
@@ -215,7 +221,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
 // the sweeps stop after one without rotations.
 template <typename T>
 __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
-                                        T rtol) {
+                                        T rtol, T* lmax_out) {
   const int lane = threadIdx.x & 31;
   const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
   const int m = (r + 1) & ~1, np = m / 2;
@@ -306,6 +312,7 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
   T lmax = T(0);
   for (int i = 0; i < r; ++i) lmax = fmax(lmax, W[i * r + i].re);
   const T cut = rtol * lmax;
+  if (lane == 0) *lmax_out = lmax;
   __syncwarp();
   for (int e = lane; e < r * r; e += 32) {
     const int i = e / r, j = e - i * r;
@@ -380,6 +387,7 @@ struct Log2<1> {
 template <typename T, int RP>
 __global__ void __launch_bounds__(kSliceThreads) k_qcon(Dev<T> d, cx<T>* __restrict__ Qout) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
   const int k = blockIdx.x;
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -466,6 +474,21 @@ __global__ void __launch_bounds__(kSliceThreads) k_qcon(Dev<T> d, cx<T>* __restr
 // One CTA per slice.  Work arrays in shared memory when they fit, else in the
 // per-slice region of d.Tb.
 // ---------------------------------------------------------------------------
+// Block-wide maximum of a non-negative value, folded into *dst (stopping test).
+__device__ __forceinline__ void block_max_to(double v, unsigned long long* dst) {
+  __shared__ double smax[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) smax[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, smax[w]);
+    atomic_max_nonneg(dst, m);
+  }
+}
+
 struct XLayout {
   size_t mats, ht, xs, qs, ts, total;
 };
@@ -573,6 +596,7 @@ __device__ __forceinline__ cx<T> hth_at(const cx<T>* x, int i, int n1) {
 template <typename T, int RP>
 __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
   const int k = blockIdx.x;
   const int n1 = d.n1, n2 = d.n2, r = d.r, rr = r * r;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -632,7 +656,9 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
     }
   }
   __syncthreads();
-  const bool certA = block_pinv_herm<T, RP>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol) != 0;
+  const bool certA = block_pinv_herm<T, RP>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0) != 0;
+  // step along d_X: 1, or alpha / L1 with L1 = ||H_rho1||_2 lambda_max(A)
+  const T t1 = d.scaled ? ((sred[2] > T(0)) ? d.alpha / (d.hnorm * sred[2]) : T(0)) : T(1);
 
   // ---- B = Q A^+ - rho1 (H^T H X~) P ------------------------------------------------------
   for (int e = tid; e < r * n1; e += blockDim.x) {
@@ -656,12 +682,16 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
     for (int s = wid; s < r; s += nw) warp_tridiag_solve<T>(Ts + (size_t)s * n1, n1, hinv, ha);
     __syncthreads();
   }
-  // ---- X~' = X~ + d_X (Ts; Xs keeps the old factor) ---------------------------------------
+  // ---- X~' = X~ + t d_X (Ts; Xs keeps the old factor) -------------------------------------
+  double dmax = 0.0;
   for (int e = tid; e < r * n1; e += blockDim.x) {
-    cx<T> v = Xs[e] + Ts[e];
+    const cx<T> x0 = Xs[e];
+    cx<T> v = (d.scaled ? x0 + Ts[e] * t1 : x0 + Ts[e]);
     if (realslice) v.im = T(0);
     Ts[e] = v;
+    if (d.conv) dmax = fmax(dmax, (double)cabs(v - x0));
   }
+  if (d.conv) block_max_to(dmax, d.conv + 0);
   __syncthreads();
 
   // ---- G = X~'^H H_rho1 X~' (Hermitian) and Dg = E - G ----------------------------------
@@ -710,10 +740,12 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
     }
   }
   __syncthreads();
-  block_pinv_herm<T, RP>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol);
-  // ---- Dg and G^+ for k_ystep; X~ <- X~' ---------------------------------------------------
+  block_pinv_herm<T, RP>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0);
+  // step along d_Y: 1, or beta / L2 with L2 = lambda_max(G), folded into G^+
+  const T t2 = d.scaled ? ((sred[2] > T(0)) ? d.beta / sred[2] : T(0)) : T(1);
+  // ---- Dg and t G^+ for k_ystep; X~ <- X~' -------------------------------------------------
   for (int e = tid; e < rr; e += blockDim.x) {
-    cx<T> gp = Ap[e];
+    cx<T> gp = Ap[e] * t2;
     if (realslice) gp.im = T(0);
     d.Dg[(size_t)k * rr + e] = Dgm[e];
     d.Gp[(size_t)k * rr + e] = gp;
@@ -739,6 +771,7 @@ template <typename T, int RP>
 __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   constexpr int CPL = ystep_cpl(RP), TW = 32 * CPL;
   extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
   const int k = blockIdx.x;
   const int j0 = blockIdx.y * TW;
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S, rr = r * r;
@@ -819,6 +852,7 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   }
   __syncthreads();
   const bool realslice = (k == 0) || (2 * k == d.n3);
+  double dmax = 0.0;
   for (int e = tid; e < RP * TW; e += blockDim.x) {
     const int s = e / TW, c = e - s * TW;
     if (s >= r || j0 + c >= n2) {
@@ -830,7 +864,9 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
     if (realslice) y.im = T(0);
     d.Yt[((size_t)k * r + s) * n2 + j0 + c] = y;
     Yn[e] = y;
+    if (d.conv) dmax = fmax(dmax, (double)cabs(y - Yo[e]));
   }
+  if (d.conv) block_max_to(dmax, d.conv + 1);
   __syncthreads();
 
   // ---- Grams of the new Y~' over each 32 columns (A of the next X-step) ----------------
@@ -868,7 +904,11 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
       }
 #pragma unroll
     for (int h = 0; h < CPL; ++h)
-      if (live[h]) zc[(size_t)i * rstride + 32 * h] = z[h];
+      if (live[h]) {
+        const size_t o = (size_t)i * rstride + 32 * h;
+        if (d.dZt) d.dZt[zc - d.Zt + o] = z[h] - zc[o];  // Z~^{l+1} - Z~^l for the stopping test
+        zc[o] = z[h];
+      }
   }
 }
 

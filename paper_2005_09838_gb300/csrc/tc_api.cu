@@ -40,12 +40,11 @@ tc_status validate(const tc_params* p) {
       return fail(TC_ERR_UNSUPPORTED, "TF32/BF16 precision is not built");
     return fail(TC_ERR_ARG, "unknown precision");
   }
-  if (p->step != TC_STEP_EXACT) {
-    if (p->step == TC_STEP_SCALED) return fail(TC_ERR_UNSUPPORTED, "scaled steps are not built");
-    return fail(TC_ERR_ARG, "unknown step rule");
-  }
+  if (p->step != TC_STEP_EXACT && p->step != TC_STEP_SCALED) return fail(TC_ERR_ARG, "unknown step rule");
+  if (p->step == TC_STEP_SCALED &&
+      (!(p->alpha > 0) || !(p->beta > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->beta)))
+    return fail(TC_ERR_ARG, "scaled steps need finite alpha > 0 and beta > 0");
   if (!(p->eps >= 0) || !std::isfinite(p->eps)) return fail(TC_ERR_ARG, "eps must be finite and >= 0");
-  if (p->eps > 0) return fail(TC_ERR_UNSUPPORTED, "the stopping test (eps > 0) is not built");
   if (!std::isfinite(p->pinv_rtol) || p->pinv_rtol >= 1.0) return fail(TC_ERR_ARG, "pinv_rtol must be < 1");
   return TC_OK;
 }
@@ -101,7 +100,7 @@ tc_status tc_iterate(tc_ctx* c, int32_t n_iters, int32_t* done) {
   if (prev != c->device) cudaSetDevice(c->device);
   std::string err;
   int d = 0;
-  tc_status st = c->eng->iterate(n_iters, &d, err);
+  tc_status st = c->eng->iterate(n_iters, done ? &d : nullptr, err);
   if (prev != c->device) cudaSetDevice(prev);
   if (done) *done = d;
   return st == TC_OK ? st : fail(st, err);
@@ -142,6 +141,22 @@ tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms) {
   std::string err;
   tc_status st = c->eng->profile(n_iters, ms, err);
   if (prev != c->device) cudaSetDevice(prev);
+  return st == TC_OK ? st : fail(st, err);
+}
+
+tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* iters_run) {
+  g_last_error.clear();
+  if (!c || !changes) return fail(TC_ERR_ARG, "ctx and changes are required");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  std::string err;
+  int s = 0;
+  long long it = 0;
+  tc_status st = c->eng->convergence(changes, &s, &it, err);
+  if (prev != c->device) cudaSetDevice(prev);
+  if (stopped) *stopped = s;
+  if (iters_run) *iters_run = it;
   return st == TC_OK ? st : fail(st, err);
 }
 

@@ -61,6 +61,12 @@ __host__ __device__ __forceinline__ void cfmaconj(cx<T>& acc, cx<T> a, cx<T> b) 
   acc.im = fma(-a.im, b.re, acc.im);
 }
 
+// |a|
+template <typename T>
+__host__ __device__ __forceinline__ T cabs(cx<T> a) {
+  return sqrt(a.re * a.re + a.im * a.im);
+}
+
 // Read-only cached load of a complex value.
 __device__ __forceinline__ cx<float> ldg_cx(const cx<float>* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));

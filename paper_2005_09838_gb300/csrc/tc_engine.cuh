@@ -159,7 +159,17 @@ class Engine final : public EngineBase {
     double* part = alloc<double>((size_t)n1_ * 4, err);
     double* part_k = alloc<double>((size_t)S_, err);
     int* derr = alloc<int>(1, err);
+    // stopping test (eps > 0): change maxima, flag, counter; |dW| partial sums; Z~ changes
+    unsigned long long* conv = nullptr;
+    double* part_dw = nullptr;
+    cx<T>* dZt = nullptr;
+    if (p.eps > 0) {
+      conv = alloc<unsigned long long>(8, err);
+      part_dw = alloc<double>((size_t)n1_, err);
+      dZt = alloc<cx<T>>((size_t)n1_ * S_ * n2_, err);
+    }
     if (!err.empty()) return TC_ERR_NOMEM;
+    if (conv) TC_CUDA_TRY(cudaMemsetAsync(conv, 0, 8 * sizeof(unsigned long long), stream_));
 
     // ---- kernel variants and shared memory -------------------------------------------
     SlabCfg<T> cfg{};
@@ -261,6 +271,16 @@ class Engine final : public EngineBase {
     d_.part_k = part_k;
     d_.err = derr;
     d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * (double)std::numeric_limits<T>::epsilon();
+    d_.scaled = (p.step == TC_STEP_SCALED) ? 1 : 0;
+    d_.alpha = (T)p.alpha;
+    d_.beta = (T)p.beta;
+    // ||H_rho1||_2 = 1 + rho1 lambda_max(H^T H); H^T H is the path Laplacian on n1
+    // nodes with lambda_max = 2 + 2 cos(pi / n1)
+    d_.hnorm = (T)(1.0 + p.rho1 * (n1_ > 1 ? 2.0 + 2.0 * std::cos(M_PI / (double)n1_) : 0.0));
+    d_.conv = conv;
+    d_.part_dw = part_dw;
+    d_.dZt = dZt;
+    d_.eps = p.eps;
     TC_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), stream_));
 
     // ---- inputs --------------------------------------------------------------------------
@@ -319,8 +339,43 @@ class Engine final : public EngineBase {
       tc_status st = capture(err);
       if (st != TC_OK) return st;
     }
+    unsigned long long h0[8] = {}, h1[8] = {};
+    if (done && d_.conv) {
+      tc_status st = read_conv(h0, err);
+      if (st != TC_OK) return st;
+    }
     for (int i = 0; i < n; ++i) TC_CUDA_TRY(cudaGraphLaunch(graph_exec_, stream_));
-    if (done) *done = n;
+    if (done) {
+      if (d_.conv) {
+        tc_status st = read_conv(h1, err);
+        if (st != TC_OK) return st;
+        *done = (int)(h1[3] - h0[3]);  // iterations run before the stopping test fired
+      } else {
+        *done = n;
+      }
+    }
+    return TC_OK;
+  }
+
+  tc_status convergence(double* changes, int* stopped, long long* iters_run, std::string& err) override {
+    if (poisoned_) {
+      err = "context poisoned by an earlier error";
+      return TC_ERR_STATE;
+    }
+    if (!d_.conv) {
+      err = "the stopping test is off (eps = 0)";
+      return TC_ERR_STATE;
+    }
+    unsigned long long h[8];
+    tc_status st = read_conv(h, err);
+    if (st != TC_OK) return st;
+    for (int q = 0; q < 3; ++q) {
+      double v;
+      std::memcpy(&v, &h[4 + q], sizeof(double));
+      changes[q] = v;
+    }
+    *stopped = h[2] != 0ull;
+    *iters_run = (long long)h[3];
     return TC_OK;
   }
 
@@ -482,6 +537,13 @@ class Engine final : public EngineBase {
     launch_xstep(s);
     launch_ystep(s);
     launch_slab(MODE_ITER, nullptr, 0, s);
+    if (d_.conv) k_check<T><<<1, 32, 0, s>>>(d_);  // step 6
+  }
+
+  tc_status read_conv(unsigned long long* h, std::string& err) {
+    TC_CUDA_TRY(cudaMemcpyAsync(h, d_.conv, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_));
+    TC_CUDA_TRY(cudaStreamSynchronize(stream_));
+    return TC_OK;
   }
 
   tc_status capture(std::string& err) {

@@ -19,6 +19,7 @@ struct EngineBase {
   virtual tc_status objective(double* f0, double* resid_obs, std::string& err) = 0;
   virtual tc_status result(void* W, void* X, void* Y, bool on_device, std::string& err) = 0;
   virtual tc_status profile(int n, double* ms, std::string& err) = 0;
+  virtual tc_status convergence(double* changes, int* stopped, long long* iters_run, std::string& err) = 0;
   virtual void release() = 0;
 };
 

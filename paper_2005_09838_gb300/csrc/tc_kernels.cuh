@@ -47,7 +47,28 @@ struct Dev {
   double* part_k;   // [S] rho1-term per slice
   int* err;
   double rtol;
+  // step control (Eq. (updataXYW1) step sizes; Algorithm step 6)
+  int scaled;        // 0: unit steps; 1: steps alpha / L1, beta / L2 (L from lambda_max)
+  T alpha, beta;
+  T hnorm;           // ||H_rho1||_2
+  unsigned long long* conv;  // stopping test (null when off): [0] max |X~' - X~|, [1] max |Y~' - Y~|
+                             // (non-negative doubles as bits), [2] stop flag, [3] iterations done,
+                             // [4..6] last ||dX~||_inf, ||dY~||_inf, ||dW||_F as double bits
+  double* part_dw;   // [n1] partial sums of ||W~^{l+1} - W~^l||^2 over the half spectrum (weighted)
+  cx<T>* dZt;        // [n1][S][n2] Z~^{l+1} - Z~^l (written by k_ystep while the test is on)
+  double eps;
 };
+
+// True once the stopping test has fired: the iteration kernels return at once.
+template <typename T>
+__device__ __forceinline__ bool converged(const Dev<T>& d) {
+  return d.conv != nullptr && *reinterpret_cast<volatile const unsigned long long*>(d.conv + 2) != 0ull;
+}
+
+// atomic max of a non-negative double (its bit pattern orders like the value)
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v) {
+  atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

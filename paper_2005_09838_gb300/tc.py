@@ -72,6 +72,9 @@ def load(path: str | None = None):
     lib.tc_result.restype = ctypes.c_int
     lib.tc_profile.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     lib.tc_profile.restype = ctypes.c_int
+    lib.tc_convergence.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int64)]
+    lib.tc_convergence.restype = ctypes.c_int
     lib.tc_complete_static.argtypes = [ctypes.POINTER(tc_params), P, P, P, P, ctypes.c_int32, P,
                                        ctypes.POINTER(ctypes.c_double), P]
     lib.tc_complete_static.restype = ctypes.c_int
@@ -126,10 +129,25 @@ class Completion:
     def dtype(self):
         return np.float64 if self.params.precision == TC_FP64 else np.float32
 
-    def iterate(self, n: int) -> int:
+    def iterate(self, n: int, count: bool = True) -> int:
+        """Run n iterations; returns the number run (fewer once the stopping
+        test of a context with eps > 0 has held).  count=False skips the
+        count (no stream synchronisation) and returns n."""
+        if not count:
+            _check(self._lib.tc_iterate(self._ctx, int(n), None))
+            return int(n)
         done = ctypes.c_int32(0)
         _check(self._lib.tc_iterate(self._ctx, int(n), ctypes.byref(done)))
         return done.value
+
+    def convergence(self):
+        """(||dX~||_inf, ||dY~||_inf, ||dW||_F) of the last iteration, whether
+        the stopping test has held, and the iterations run since init."""
+        ch = (ctypes.c_double * 3)()
+        stopped = ctypes.c_int32(0)
+        it = ctypes.c_int64(0)
+        _check(self._lib.tc_convergence(self._ctx, ch, ctypes.byref(stopped), ctypes.byref(it)))
+        return tuple(ch), bool(stopped.value), int(it.value)
 
     def objective(self):
         f0 = ctypes.c_double()

@@ -65,8 +65,10 @@ def test_params_layout_matches_header(tmp_path):
     (dict(rho2=float("nan")), "TC_ERR_ARG"),
     (dict(precision=2), "TC_ERR_UNSUPPORTED"),
     (dict(precision=9), "TC_ERR_ARG"),
-    (dict(step=1), "TC_ERR_UNSUPPORTED"),
-    (dict(eps=1e-6), "TC_ERR_UNSUPPORTED"),
+    (dict(step=1, alpha=0.0), "TC_ERR_ARG"),     # scaled steps need alpha, beta > 0
+    (dict(step=1, beta=float("inf")), "TC_ERR_ARG"),
+    (dict(step=2), "TC_ERR_ARG"),
+    (dict(eps=-1e-6), "TC_ERR_ARG"),
 ])
 def test_invalid_arguments_are_rejected_on_the_host(lib, kw, status):
     from paper_2005_09838_gb300 import tc

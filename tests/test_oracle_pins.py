@@ -372,3 +372,77 @@ def test_dense_and_banded_wstep_agree_in_the_loop():
     a = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 0.1, 0.5, inst["Y0"], iters=4, wstep="dense")
     b = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 0.1, 0.5, inst["Y0"], iters=4, wstep="kkt")
     np.testing.assert_allclose(a["W"], b["W"], rtol=1e-11, atol=1e-11)
+
+
+def test_stopping_test_ends_at_the_first_iteration_meeting_all_three_bounds():
+    # Algorithm step 6: stop after the first iteration l with ||X~' - X~||_inf,
+    # ||Y~' - Y~||_inf and ||W' - W||_F all <= eps
+    w = wl.custom(8, 12, 5, 2, 0.5, seed=77)
+    inst = wl.generate(w)
+    full = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 1e-3, 1e-1, inst["Y0"], iters=30, record=True)
+    h = full["hist"]
+    m = np.maximum(np.maximum(h["dX"], h["dY"]), h["dW"])
+    for eps in (m[3] * 1.0000001, m[7], 0.5 * (m[10] + m[11])):
+        first = next(i for i in range(30) if m[i] <= eps) + 1
+        out = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 1e-3, 1e-1, inst["Y0"], iters=30, eps=eps)
+        assert out["iters"] == first
+        short = O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 1e-3, 1e-1, inst["Y0"], iters=first)
+        assert np.array_equal(out["W"], short["W"])
+    assert O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 1e-3, 1e-1, inst["Y0"], iters=6, eps=0.0)["iters"] == 6
+    assert O.tctf2r(inst["G"], inst["mask"], 2, 1e-3, 1e-3, 1e-1, inst["Y0"], iters=6, eps=1e300)["iters"] == 1
+
+
+# ---------------------------------------------------------------------------
+# Differentiation form: loss of the factors and its gradient
+# ---------------------------------------------------------------------------
+
+def _grad_case(m1=12, m2=24, m3=8, r=3, seed=11):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m1, r, m3))
+    Y = rng.standard_normal((r, m2, m3))
+    G = rng.standard_normal((m1, m2, m3))
+    mask = rng.random((m1, m2, m3)) < 0.3
+    return X, Y, G, mask
+
+
+def test_conjugate_transpose_reverses_the_t_product():
+    # (A*B)^* = B^* * A^* and (A^*)^* = A, with the t-product by its definition
+    rng = np.random.default_rng(5)
+    A, B = rng.standard_normal((4, 3, 6)), rng.standard_normal((3, 5, 6))
+    lhs = O.ttranspose(O.tprod_definition(A, B))
+    rhs = O.tprod_definition(O.ttranspose(B), O.ttranspose(A))
+    assert np.allclose(lhs, rhs, rtol=0, atol=1e-12)
+    assert np.array_equal(O.ttranspose(O.ttranspose(A)), A)
+
+
+@pytest.mark.parametrize("rho1", [0.0, 0.3])
+def test_factor_loss_gradient_matches_central_differences(rho1):
+    # L is quadratic in any single entry of X (or of Y), so a central
+    # difference equals the partial derivative up to rounding
+    X, Y, G, mask = _grad_case()
+    gX, gY = O.factor_loss_grad(X, Y, G, mask, rho1)
+    h = 1e-3
+    rng = np.random.default_rng(3)
+    for A, g in ((X, gX), (Y, gY)):
+        for _ in range(12):
+            idx = tuple(int(rng.integers(0, n)) for n in A.shape)
+            old = A[idx]
+            A[idx] = old + h
+            fp = O.factor_loss(X, Y, G, mask, rho1)
+            A[idx] = old - h
+            fm = O.factor_loss(X, Y, G, mask, rho1)
+            A[idx] = old
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - g[idx]) <= 1e-7 * max(1.0, abs(g[idx]))
+
+
+def test_factor_loss_gradient_with_one_slice_is_the_matrix_gradient():
+    # m3 = 1: L = 1/2 ||P(XY - G)||^2 + rho1/2 ||H X Y||^2, dL/dX = E Y^T, dL/dY = X^T E
+    X, Y, G, mask = _grad_case(m3=1)
+    rho1 = 0.2
+    x, y, g, m = X[:, :, 0], Y[:, :, 0], G[:, :, 0], mask[:, :, 0]
+    D = O.toeplitz_D(x.shape[0])
+    E = np.where(m, x @ y - g, 0.0) + rho1 * D.T @ D @ x @ y
+    gX, gY = O.factor_loss_grad(X, Y, G, mask, rho1)
+    assert np.allclose(gX[:, :, 0], E @ y.T, rtol=1e-12, atol=1e-12)
+    assert np.allclose(gY[:, :, 0], x.T @ E, rtol=1e-12, atol=1e-12)
