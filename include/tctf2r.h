@@ -143,6 +143,32 @@ tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
  * TC_ERR_CUDA. */
 tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* iters_run);
 
+/* Differentiation form: the factor terms of f0 (Eq. (TETP-optim)) with W held
+ * at G on the mask, as a loss of spatial factors X (n1 x r x n3) and Y
+ * (r x n2 x n3),
+ *   L(X, Y) = 1/2 ||P_Omega(X*Y - G)||_F^2 + rho1/2 ||H unfold(X*Y, 1)||_F^2,
+ * and its gradient, by the adjoint of the t-product (conjugate transpose of
+ * Sec. 2): with E = P_Omega(Z - G) + rho1 (H^T H) x_1 Z, Z = X*Y,
+ *   dL/dX = E * Y^*,  dL/dY = X^* * E,
+ * evaluated per slice of the half spectrum (Eq. (bar BA-k), Eq. (barAAk)).
+ * The gradients are those of Eq. (hkXYDer) gathered over the slices.
+ *
+ * tc_grad_init: p gives n1, n2, n3, r, rho1 and precision (TC_FP64 or TC_FP32;
+ *   mu, rho2, step, eps are not used); G and mask as for tc_init (copied).
+ * tc_grad_eval: X, Y in the precision's type, column-major (i1 fastest) like
+ *   X0, Y0 of tc_init; loss receives L in FP64 (required); dX, dY receive the
+ *   gradients in the layouts of X, Y (each may be NULL: then it is not
+ *   formed).  on_device selects device or host buffers for X, Y, dX, dY.
+ *   Synchronises the stream.  Errors: TC_ERR_ARG, TC_ERR_CUDA,
+ *   TC_ERR_NUMERIC (non-finite loss).
+ * tc_grad_free: NULL-safe. */
+typedef struct tc_grad tc_grad;
+tc_status tc_grad_init(tc_grad** out, const tc_params* p, const void* G, const uint8_t* mask,
+                       int32_t inputs_on_device, void* cuda_stream);
+tc_status tc_grad_eval(tc_grad* g, const void* X, const void* Y, double* loss, void* dX, void* dY,
+                       int32_t on_device);
+tc_status tc_grad_free(tc_grad* g);
+
 /* Allocation-free completion of a small tensor (this entry point has no
  * counterpart in the paper; it is a deployment aid).  Some callers cannot call
  * cudaMalloc: code hosted in a framework whose allocator owns the device

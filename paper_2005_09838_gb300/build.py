@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libtctf2r.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["tc_api.cu", "tc_f32.cu", "tc_f32_112.cu", "tc_f32_168.cu", "tc_f64.cu", "tc_static.cu"]
+SOURCES = ["tc_api.cu", "tc_f32.cu", "tc_f32_112.cu", "tc_f32_168.cu", "tc_f64.cu", "tc_static.cu", "tc_grad.cu"]
 
 
 def nvcc() -> str:

@@ -12,7 +12,7 @@
 
 namespace tc {
 
-enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2 };
+enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2, MODE_GRAD = 3 };
 
 // Threads per CTA: the register transforms and the W-step sweeps need the
 // 255-register budget of two warps per scheduler (nine warps would put three
@@ -246,7 +246,7 @@ __device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, 
       acc.im += x * w.im;
     }
     if (k == 0 || (2 * k == n3)) acc.im = T(0);
-    const cx<T> rn = acc - zsub[k * stride];
+    const cx<T> rn = zsub ? acc - zsub[k * stride] : acc;
     if (dz) dw2 += dw_term(rn, out[k * stride], dz[k * stride], k, n3);
     out[k * stride] = rn;
   }
@@ -301,9 +301,11 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   }
 
   // ---- phase A: inverse transform of each tube; v = G on the mask ------------
+  // (MODE_GRAD: v = Z - G on the mask, 0 elsewhere; gsum = ||v||^2)
+  double gsum = 0.0;
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
-    if (MODE == MODE_ITER) {
+    if (MODE == MODE_ITER || MODE == MODE_GRAD) {
       // G (row-major, read coalesced) is staged into the slab, transposed to the
       // tube-major layout, with asynchronous copies issued ahead of the transforms;
       // each tube then picks its observed values from its own column.
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
 #pragma unroll
       for (int k = 0; k < SL; ++k) {
         const size_t o = (size_t)k * n2 + (act ? t : 0);
-        if (MODE == MODE_ITER) X[k] = ldg_cx(zrow + o);
+        if (MODE == MODE_ITER || MODE == MODE_GRAD) X[k] = ldg_cx(zrow + o);
         else if (MODE == MODE_W) X[k] = ldg_cx(zrow + o) + ldg_cx(rrow + o);
         else X[k] = ldg_cx(rrow + o);
       }
@@ -351,6 +353,14 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
           const bool ob = act && ((msk[l * mwords + (ta >> 5)] >> (ta & 31)) & 1u);
           x[l] = ob ? spat[(size_t)ta * LP + l] : x[l] * zfac;
         }
+      } else if (MODE == MODE_GRAD) {
+        const int ta = act ? t : 0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          const bool ob = act && ((msk[l * mwords + (ta >> 5)] >> (ta & 31)) & 1u);
+          x[l] = ob ? x[l] - spat[(size_t)ta * LP + l] : T(0);
+          gsum += (double)x[l] * (double)x[l];
+        }
       }
       if (act) {
 #pragma unroll
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       for (int k = 0; k < S; ++k) {
         const size_t o = (size_t)k * n2 + t;
         cx<T> v;
-        if (MODE == MODE_ITER) v = zrow[o];
+        if (MODE == MODE_ITER || MODE == MODE_GRAD) v = zrow[o];
         else if (MODE == MODE_W) v = zrow[o] + rrow[o];
         else v = rrow[o];
         spec[k * n2 + t] = v;
@@ -376,6 +386,12 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
         for (int l = 0; l < n3; ++l) {
           const bool ob = (msk[l * mwords + (t >> 5)] >> (t & 31)) & 1u;
           col[l] = ob ? __ldg(Gi + (size_t)l * n2 + t) : col[l] * zfac;
+        }
+      } else if (MODE == MODE_GRAD) {
+        for (int l = 0; l < n3; ++l) {
+          const bool ob = (msk[l * mwords + (t >> 5)] >> (t & 31)) & 1u;
+          col[l] = ob ? col[l] - __ldg(Gi + (size_t)l * n2 + t) : T(0);
+          gsum += (double)col[l] * (double)col[l];
         }
       }
     }
@@ -414,7 +430,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   }
 
   // ---- phase C: forward transform, R~ = W~ - Z~ ------------------------------
-  const bool track = !init && d.dZt != nullptr;
+  const bool track = (MODE == MODE_ITER) && !init && d.dZt != nullptr;
   double dw2 = 0.0;
   if constexpr (L > 0) {
     constexpr int SL = L / 2 + 1;
@@ -428,7 +444,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       const cx<T>* zt = zrow + t;
 #pragma unroll
       for (int k = 0; k < SL; ++k) {
-        const cx<T> rn = X[k] - ldg_cx(zt + (size_t)k * n2);
+        const cx<T> rn = (MODE == MODE_GRAD) ? X[k] : X[k] - ldg_cx(zt + (size_t)k * n2);
         if (track) dw2 += dw_term(rn, rt[(size_t)k * n2], d.dZt[(size_t)i1 * SL * n2 + (size_t)k * n2 + t], k, L);
         rt[(size_t)k * n2] = rn;
       }
@@ -436,14 +452,19 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
   } else {
     for (int t = tid; t < n2; t += nt) {
       const size_t o = (size_t)i1 * S * n2 + t;
-      generic_rdft_sub<T>(spat + (size_t)t * LP, zrow + t, d.Rt + o, (size_t)n2, n3, d.twg,
-                          track ? d.dZt + o : nullptr, dw2);
+      generic_rdft_sub<T>(spat + (size_t)t * LP, (MODE == MODE_GRAD) ? nullptr : zrow + t, d.Rt + o, (size_t)n2,
+                          n3, d.twg, track ? d.dZt + o : nullptr, dw2);
     }
   }
   if (track) {
     double unused = 0.0;
     block_sum2(dw2, unused, red);
     if (tid == 0) d.part_dw[i1] = dw2;
+  }
+  if (MODE == MODE_GRAD) {
+    double unused = 0.0;
+    block_sum2(gsum, unused, red);
+    if (tid == 0) d.part[(size_t)i1 * 4] = gsum;
   }
 }
 

@@ -25,6 +25,8 @@
 //   MODE_W     W = iDFT(Z~ + R~): optional copy to Wout (column-major),
 //              partial sums ||W||^2 and ||K unfold(W,2)||^2.
 //   MODE_R     R = iDFT(R~): partial sums ||R||^2 and ||P_Omega R||^2.
+//   MODE_GRAD  differentiation form: E = P_Omega(iDFT(Z~) - G) and R~ = DFT(E)
+//              stored, partial sum ||E||^2 (the masked loss).
 #pragma once
 
 namespace tc {
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   if (MODE != MODE_W) {
     // the half spectrum lands in slots 0..M of every tube through asynchronous
     // copies (all in flight at once), then is split in place
-    const cx<T>* src = (MODE == MODE_ITER) ? zrow : rrow;
+    const cx<T>* src = (MODE == MODE_ITER || MODE == MODE_GRAD) ? zrow : rrow;
     ItemIter it(tid, n2);
     for (int e = tid; e < (M + 1) * n2; e += nt, it.advance(nt, n2))
       cp_async_elem(reinterpret_cast<cx<T>*>(buf + (size_t)it.t * LP) + it.g, src + e);
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
   // ---- A3: inverse DFT_N2 over slots N2 k1 + j -> spatial values; v = G on the mask -------
   // (the G values of the next item are loaded while the current one is computed)
   const T scale = T(1) / T(M);
+  double gsum = 0.0;  // MODE_GRAD: ||E||^2 partial
   {
     T gn[2 * N2];
     auto load_g = [&](int k1, int t) {
@@ -213,13 +216,14 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
       }
     };
     ItemIter it(tid, n2);
-    if (MODE == MODE_ITER && tid < N1 * n2) load_g(it.g, it.t);
+    constexpr bool NEED_G = (MODE == MODE_ITER || MODE == MODE_GRAD);
+    if (NEED_G && tid < N1 * n2) load_g(it.g, it.t);
     for (int e = tid; e < N1 * n2; e += nt) {
       const int k1 = it.g, t = it.t;
       it.advance(nt, n2);
       T* tb = buf + (size_t)t * LP + 2 * N2 * k1;
       T g[2 * N2];
-      if (MODE == MODE_ITER) {
+      if (NEED_G) {
 #pragma unroll
         for (int q = 0; q < 2 * N2; ++q) g[q] = gn[q];
         if (e + nt < N1 * n2) load_g(it.g, it.t);
@@ -236,6 +240,12 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
           const uint32_t w0 = msk[l * mw + (t >> 5)], w1 = msk[(l + 1) * mw + (t >> 5)];
           x0 = ((w0 >> (t & 31)) & 1u) ? g[2 * k2] : x0 * zfac;
           x1 = ((w1 >> (t & 31)) & 1u) ? g[2 * k2 + 1] : x1 * zfac;
+        } else if (MODE == MODE_GRAD) {
+          const int l = 2 * (k1 + N1 * k2);
+          const uint32_t w0 = msk[l * mw + (t >> 5)], w1 = msk[(l + 1) * mw + (t >> 5)];
+          x0 = ((w0 >> (t & 31)) & 1u) ? x0 - g[2 * k2] : T(0);
+          x1 = ((w1 >> (t & 31)) & 1u) ? x1 - g[2 * k2 + 1] : T(0);
+          gsum += (double)x0 * (double)x0 + (double)x1 * (double)x1;
         }
         st_slot(tb, k2, cx<T>{x0, x1});
       }
@@ -314,7 +324,7 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
 
   // ---- C3: split to the half spectrum; R~ = W~ - Z~ ------------------------------------------
   cx<T>* rt = d.Rt + (size_t)i1 * (M + 1) * n2;
-  const bool track = !init && d.dZt != nullptr;
+  const bool track = (MODE == MODE_ITER) && !init && d.dZt != nullptr;
   const cx<T>* dz = track ? d.dZt + (size_t)i1 * (M + 1) * n2 : nullptr;
   double dw2 = 0.0;
   {
@@ -324,7 +334,8 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
       const int kc = M - k;
       const T* tb = buf + (size_t)t * LP;
       const size_t ok = (size_t)k * n2 + t, oc = (size_t)kc * n2 + t;
-      const cx<T> zk0 = ldg_cx(zrow + ok), zc0 = ldg_cx(zrow + oc);
+      const cx<T> zk0 = (MODE == MODE_GRAD) ? cx<T>{T(0), T(0)} : ldg_cx(zrow + ok);
+      const cx<T> zc0 = (MODE == MODE_GRAD) ? cx<T>{T(0), T(0)} : ldg_cx(zrow + oc);
       cx<T> rk, rc;
       if (k == 0) {
         const cx<T> z0 = ld_slot(tb, 0);
@@ -347,6 +358,11 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
     double unused = 0.0;
     block_sum2(dw2, unused, red);
     if (tid == 0) d.part_dw[i1] = dw2;
+  }
+  if (MODE == MODE_GRAD) {
+    double unused = 0.0;
+    block_sum2(gsum, unused, red);
+    if (tid == 0) d.part[(size_t)i1 * 4] = gsum;
   }
 }
 

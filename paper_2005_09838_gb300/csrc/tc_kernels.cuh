@@ -120,3 +120,4 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 #include "k_slab_f.cuh"
 #include "k_slice.cuh"
 #include "k_aux.cuh"
+#include "k_grad.cuh"

@@ -78,6 +78,12 @@ def load(path: str | None = None):
     lib.tc_complete_static.argtypes = [ctypes.POINTER(tc_params), P, P, P, P, ctypes.c_int32, P,
                                        ctypes.POINTER(ctypes.c_double), P]
     lib.tc_complete_static.restype = ctypes.c_int
+    lib.tc_grad_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(tc_params), P, P, ctypes.c_int32, P]
+    lib.tc_grad_init.restype = ctypes.c_int
+    lib.tc_grad_eval.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_double), P, P, ctypes.c_int32]
+    lib.tc_grad_eval.restype = ctypes.c_int
+    lib.tc_grad_free.argtypes = [P]
+    lib.tc_grad_free.restype = ctypes.c_int
     lib.tc_free.argtypes = [P]
     lib.tc_free.restype = ctypes.c_int
     lib.tc_last_error.argtypes = []
@@ -176,6 +182,42 @@ class Completion:
     def close(self):
         if self._ctx:
             self._lib.tc_free(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class GradContext:
+    """Differentiation form (tc_grad_*): loss of the factor model and its
+    gradient.  X (n1*r*n3) and Y (r*n2*n3) in the column-major layout of
+    tc_init's X0, Y0, as numpy arrays or torch tensors."""
+
+    def __init__(self, params: tc_params, G, mask, on_device: bool = False, stream: int | None = None):
+        self._lib = load()
+        self.params = params
+        self._ctx = ctypes.c_void_p()
+        _check(self._lib.tc_grad_init(ctypes.byref(self._ctx), ctypes.byref(params), _ptr(G), _ptr(mask),
+                                      1 if on_device else 0, stream))
+
+    def eval(self, X, Y, dX=None, dY=None, on_device: bool = False) -> float:
+        loss = ctypes.c_double()
+        _check(self._lib.tc_grad_eval(self._ctx, _ptr(X), _ptr(Y), ctypes.byref(loss), _ptr(dX), _ptr(dY),
+                                      1 if on_device else 0))
+        return loss.value
+
+    def close(self):
+        if self._ctx:
+            self._lib.tc_grad_free(self._ctx)
             self._ctx = ctypes.c_void_p()
 
     def __del__(self):
