@@ -17,7 +17,7 @@
  *    (i1, i2, i3) of an n1 x n2 x n3 tensor is at i1 + n1*(i2 + n2*i3).  This
  *    is the element order of the paper's unfold (Sec. 2.1).
  *  - Real element type follows tc_params.precision: double for TC_FP64,
- *    float for TC_FP32.
+ *    float for TC_FP32, TC_TF32 and TC_BF16.
  *  - The caller owns every pointer it passes; the library copies what it
  *    needs and never keeps a caller pointer past the call.
  *  - A context is bound to the CUDA device that was current at tc_init and to
@@ -46,7 +46,24 @@ typedef enum {
   TC_ERR_UNSUPPORTED = 7  /* option not implemented by this build */
 } tc_status;
 
+/* Arithmetic of the iteration.
+ *  TC_FP64, TC_FP32: every step in that type (the r x r pseudo-inverses too).
+ *  TC_TF32, TC_BF16 (the precision form; data and state in float): for
+ *    r > 16 the slice contractions Q = R~Y~^H run on the tensor cores with
+ *    operands rounded to TF32 (BF16) and FP32 accumulation, each operand
+ *    split into a rounded part and a rounded remainder (three products per
+ *    step) unless TC_FLAG_SINGLE_PASS is set; for every r the two r x r
+ *    Gram pseudo-inverses of each slice are taken in FP64.  Everything else
+ *    runs in FP32. */
 typedef enum { TC_FP64 = 0, TC_FP32 = 1, TC_TF32 = 2, TC_BF16 = 3 } tc_precision;
+
+/* tc_params.flags bits. */
+enum {
+  /* TC_TF32 / TC_BF16 only: operands rounded once (one product per step);
+   * faster, with the rounding error of the format (2^-11 TF32, 2^-8 BF16)
+   * in every contraction. */
+  TC_FLAG_SINGLE_PASS = 1
+};
 
 /* Step rule of Eq. (updataXYW1).  TC_STEP_EXACT takes alpha_kl = L_k1 and
  * beta_kl = L_k2 (unit steps along d_X, d_Y: exact minimisation of the
@@ -62,17 +79,20 @@ typedef enum { TC_STEP_EXACT = 0, TC_STEP_SCALED = 1 } tc_step;
 typedef struct {
   int64_t n1, n2, n3;  /* tensor sizes (paper m1, m2, m3), each >= 1 */
   int32_t r;           /* tubal rank, 1 <= r <= min(n1, n2, 32) */
-  int32_t precision;   /* tc_precision: TC_FP64 or TC_FP32 in this build */
+  int32_t precision;   /* tc_precision */
   double mu;           /* weight of ||W||^2, >= 0 (Eq. (TETP-optim)) */
   double rho1;         /* weight of the temporal-stability term on mode 1, >= 0 */
   double rho2;         /* weight of the periodicity term on mode 2, >= 0 */
   int32_t step;        /* tc_step */
-  int32_t flags;       /* reserved, must be 0 */
+  int32_t flags;       /* TC_FLAG_* bits; 0 for TC_FP64 and TC_FP32 */
   double alpha, beta;  /* step sizes, used only with TC_STEP_SCALED, > 0 */
   double eps;          /* stopping tolerance of step 6; 0 = run exactly n iterations */
   double pinv_rtol;    /* Gram eigenvalues <= pinv_rtol * lambda_max are cut by the
                           pseudo-inverse; <= 0 selects r times the machine epsilon
-                          of the working precision (2^-52 FP64, 2^-23 FP32) */
+                          of the solve precision: 2^-52 for TC_FP64, for the
+                          precision form and for TC_FP32 with r > 16 (whose r x r
+                          solves are carried in FP64 storage with double-FP32
+                          arithmetic), 2^-23 for TC_FP32 with r <= 16 */
 } tc_params;
 
 typedef struct tc_ctx tc_ctx;
@@ -142,6 +162,33 @@ tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
  * Errors: TC_ERR_ARG (changes NULL), TC_ERR_STATE (eps = 0 or poisoned),
  * TC_ERR_CUDA. */
 tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* iters_run);
+
+/* Batched form: many independent completions (contexts of any sizes and either
+ * precision, on the current device) advanced together, one CUDA graph launch
+ * per iteration.  The graph holds each instance's captured iteration in K
+ * independent chains, instance i in chain i mod K, so small instances that
+ * leave most of the GPU idle fill it
+ * together; the slices and tubes of every instance are independent
+ * (Eq. (BDFT): the t-product separates by slice), so no instance waits on
+ * another.  The first iterations of tc_batch_iterate time each candidate K
+ * in {1, 4, 16, count} (every trial is a real iteration of all instances,
+ * with identical results for every K) and keep the fastest.
+ *
+ * tc_batch_create: ctxs holds count distinct contexts (the caller keeps
+ *   ownership; they must outlive the batch); cuda_stream is the stream the
+ *   batch launches on.
+ * tc_batch_iterate: n_iters iterations of every instance.  Ordered after the
+ *   work queued on each context's stream and before its later calls; with a
+ *   context whose p->eps > 0 the stopping test applies to that instance.
+ *   Synchronises only while the tuning trials run.
+ * tc_batch_branches: receives the chosen K (0 while tuning).
+ * tc_batch_free: NULL-safe; the contexts stay valid.
+ * Errors: TC_ERR_ARG, TC_ERR_STATE (poisoned context), TC_ERR_CUDA. */
+typedef struct tc_batch tc_batch;
+tc_status tc_batch_create(tc_batch** out, tc_ctx* const* ctxs, int32_t count, void* cuda_stream);
+tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters);
+tc_status tc_batch_branches(tc_batch* b, int32_t* branches);
+tc_status tc_batch_free(tc_batch* b);
 
 /* Differentiation form: the factor terms of f0 (Eq. (TETP-optim)) with W held
  * at G on the mask, as a loss of spatial factors X (n1 x r x n3) and Y

@@ -20,17 +20,21 @@ def _from_colmajor(flat: np.ndarray, shape) -> np.ndarray:
 
 
 def complete(G, mask, Y0, r, iters, mu=0.0, rho1=0.0, rho2=0.0, precision="fp32", X0=None,
-             want_factors=False, objective=True, step="exact", alpha=1.0, beta=1.0, eps=0.0):
+             want_factors=False, objective=True, step="exact", alpha=1.0, beta=1.0, eps=0.0,
+             single_pass=False):
     """Run up to ``iters`` TCTF2R iterations on the GPU (fewer when ``eps`` > 0
     and the stopping test holds).  Returns a dict with W (and X, Y spatial with
     ``want_factors``), f0, resid_obs, the iterations run and, with ``eps`` > 0,
-    the last changes (||dX~||_inf, ||dY~||_inf, ||dW||_F)."""
-    prec = {"fp32": tc.TC_FP32, "fp64": tc.TC_FP64}[precision]
+    the last changes (||dX~||_inf, ||dY~||_inf, ||dW||_F).  ``precision`` is
+    "fp64", "fp32", or the precision form "tf32" / "bf16" (float data; see
+    tc_precision in the C header), where ``single_pass`` rounds the tensor-core
+    operands once instead of splitting them."""
+    prec = {"fp32": tc.TC_FP32, "fp64": tc.TC_FP64, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16}[precision]
     dt = np.float64 if prec == tc.TC_FP64 else np.float32
     n1, n2, n3 = G.shape
     st = {"exact": tc.TC_STEP_EXACT, "scaled": tc.TC_STEP_SCALED}[step]
     p = tc.make_params(n1, n2, n3, r, mu=mu, rho1=rho1, rho2=rho2, precision=prec, step=st, alpha=alpha,
-                       beta=beta, eps=eps)
+                       beta=beta, eps=eps, flags=tc.TC_FLAG_SINGLE_PASS if single_pass else 0)
     g = _colmajor(G, dt)
     m = _colmajor(np.asarray(mask, dtype=bool), np.uint8)
     y = _colmajor(Y0, dt)

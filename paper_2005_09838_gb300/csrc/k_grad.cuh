@@ -23,9 +23,13 @@ __global__ void __launch_bounds__(kYThreads) k_dcon(Dev<T> d, cx<T>* __restrict_
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   cx<T>* red = reinterpret_cast<cx<T>*>(smem);  // [nw][RP][32]
-  cx<T>* Xs = red + nw * RP * 32;               // [r][n1]
   const cx<T>* Xg = d.Xt + (size_t)k * r * n1;
-  for (int e = tid; e < r * n1; e += blockDim.x) Xs[e] = Xg[e];
+  const cx<T>* Xs = Xg;                         // [r][n1], staged when it fits
+  if (!d.yx_global) {
+    cx<T>* xs = red + nw * RP * 32;
+    for (int e = tid; e < r * n1; e += blockDim.x) xs[e] = Xg[e];
+    Xs = xs;
+  }
   __syncthreads();
   const int j = j0 + lane;
   cx<T> acc[RP];
@@ -65,8 +69,8 @@ __global__ void __launch_bounds__(kYThreads) k_dcon(Dev<T> d, cx<T>* __restrict_
 }
 
 template <typename T>
-__host__ inline size_t dcon_smem_bytes(int n1, int r, int rp) {
-  return ((size_t)(kYThreads / 32) * rp * 32 + (size_t)r * n1) * sizeof(cx<T>);
+__host__ inline size_t dcon_smem_bytes(int n1, int r, int rp, bool x_in_smem = true) {
+  return ((size_t)(kYThreads / 32) * rp * 32 + (x_in_smem ? (size_t)r * n1 : 0)) * sizeof(cx<T>);
 }
 
 // The rho1 terms, one CTA per slice, added in place:

@@ -16,8 +16,7 @@ namespace tc {
 // exactly I.  r <= 16: one warp with the matrix in registers, bound
 // ||A||_F ||A^-1||_F < 1/(2 rtol) (lambda_max <= ||A||_F, 1/lambda_min =
 // ||A^-1||_2 <= ||A^-1||_F; at that size the computed inverse is within a
-// few percent of the true one).  Larger r: the block, bound
-// ||A||_1 ||A^-1||_1 < 1/(10 rtol) (1-norms bounded through |re| + |im|).
+// few percent of the true one).  Larger r: the block, same bound.
 // Otherwise warp 0 runs a parallel cyclic Jacobi eigendecomposition
 // (round-robin pairs, r/2 rotations at a time) that applies the cutoff rule
 // literally.
@@ -30,17 +29,18 @@ template <typename T>
 __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
                                         T rtol, T* lmax_out);
 
+// Frobenius norm of the r x r block at column col0 of a row-major matrix with
+// leading dimension ld, by one warp.
 template <typename T>
-__device__ inline T warp_norm1_bound(const cx<T>* M, int ld, int col0, int r) {
+__device__ inline T warp_frob(const cx<T>* M, int ld, int col0, int r) {
   const int lane = threadIdx.x & 31;
-  T nrm = T(0);
-  for (int j = lane; j < r; j += 32) {
-    T s = T(0);
-    for (int i = 0; i < r; ++i) s += fabs(M[i * ld + col0 + j].re) + fabs(M[i * ld + col0 + j].im);
-    nrm = fmax(nrm, s);
+  T s = T(0);
+  for (int e = lane; e < r * r; e += 32) {
+    const cx<T> v = M[(e / r) * ld + col0 + e % r];
+    s += v.re * v.re + v.im * v.im;
   }
-  for (int o = 16; o > 0; o >>= 1) nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
-  return nrm;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return sqrt(s);
 }
 
 // 1/a.  FP64: a correctly rounded FP32 seed and two Newton steps
@@ -62,30 +62,133 @@ __device__ __forceinline__ T tiny_pivot() {
   return sizeof(T) == 8 ? T(1e-300) : T(1e-37f);
 }
 
-// Gauss-Jordan on W = [A | I] (r x 2r, row-major) by the threads [t0, t0 + nt)
-// of the caller; sync() orders the steps among them.  Returns 0 when a pivot
-// is not positive.
+// In-place Gauss-Jordan inverse of the r x r matrix W (row-major) without
+// pivoting: at pivot p, a_pp <- 1/a_pp, a_pj <- a_pj / a_pp, a_ij <- a_ij -
+// a_ip a_pj and a_ip <- -a_ip / a_pp (r^3 complex multiply-adds, half of the
+// augmented form).  Threads [t0, t0 + nt) of the caller; sync() orders the
+// steps among them.  Returns 0 when a pivot is not positive.
 template <typename T, typename Sync>
-__device__ __forceinline__ int gauss_jordan(cx<T>* W, cx<T>* piv, int r, int t, int nt, Sync sync) {
-  const int n2c = 2 * r;
+__device__ __forceinline__ int gauss_jordan_inplace(cx<T>* W, cx<T>* piv, int r, int t, int nt, Sync sync) {
   cx<T>* colp = piv;
   cx<T>* rowp = piv + r;
   for (int p = 0; p < r; ++p) {
-    const T pv = W[p * n2c + p].re;
+    const T pv = W[p * r + p].re;
     if (!((pv > tiny_pivot<T>()) && isfinite(pv))) return 0;
     const T ip = rcp_refined(pv);
-    for (int e = t; e < r + n2c; e += nt) {
-      if (e < r) colp[e] = W[e * n2c + p];
-      else rowp[e - r] = W[p * n2c + (e - r)] * ip;
+    for (int e = t; e < 2 * r; e += nt) {
+      if (e < r) {
+        colp[e] = W[e * r + p];
+      } else {
+        const int j = e - r;
+        rowp[j] = (j == p) ? cx<T>{ip, T(0)} : W[p * r + j] * ip;
+      }
     }
     sync();
-    for (int e = t; e < r * n2c; e += nt) {
-      const int i = e / n2c, j = e - i * n2c;
-      W[e] = (i == p) ? rowp[j] : W[e] - cmul(colp[i], rowp[j]);
+    for (int e = t; e < r * r; e += nt) {
+      const int i = e / r, j = e - i * r;
+      cx<T> v;
+      if (i == p) v = rowp[j];
+      else if (j == p) v = colp[i] * (-ip);
+      else v = W[e] - cmul(colp[i], rowp[j]);
+      W[e] = v;
     }
     sync();
   }
   return 1;
+}
+
+// Double-FP32 ("df64") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2,
+// about 48 significant bits on the FP32 pipes (Dekker's and Knuth's
+// error-free sum and product; the product's error term from an FMA).  Used
+// for the r x r inverses of FP32 engines, where FP64 units are too slow.
+struct df {
+  float hi, lo;
+};
+struct alignas(16) dfc {
+  df re, im;
+};
+__device__ __forceinline__ df df_from(double x) {
+  const float h = (float)x;
+  return df{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_norm(float s, float e) {
+  const float h = s + e;
+  return df{h, e - (h - s)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  return df_norm(s, e);
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
+  return df_norm(p, e);
+}
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return dfc{df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return dfc{df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+__device__ __forceinline__ dfc dfc_scale(dfc a, df s) { return dfc{df_mul(a.re, s), df_mul(a.im, s)}; }
+// 1/a for a > 0: FP32 reciprocal y0, then one Newton step y0 + y0 (1 - a y0)
+// in df64 (the error squares: about 2^-46 relative).
+__device__ __forceinline__ df df_rcp(df a) {
+  const float y0 = 1.0f / a.hi;
+  const df e = df_add(df{1.0f, 0.0f}, df_neg(df_mul(a, df{y0, 0.0f})));
+  return df_add(df{y0, 0.0f}, df_mul(df{y0, 0.0f}, e));
+}
+
+// gauss_jordan_inplace on an FP64 matrix, with the arithmetic in df64 (the
+// matrix is converted in place, eliminated and converted back; no FP64
+// instruction in the elimination itself).
+template <typename Sync>
+__device__ __forceinline__ int gauss_jordan_inplace_df(cx<double>* W64, cx<double>* piv, int r, int t, int nt,
+                                                       Sync sync) {
+  dfc* W = reinterpret_cast<dfc*>(W64);
+  dfc* colp = reinterpret_cast<dfc*>(piv);
+  dfc* rowp = colp + r;
+  for (int e = t; e < r * r; e += nt) {
+    const cx<double> v = W64[e];
+    W[e] = dfc{df_from(v.re), df_from(v.im)};
+  }
+  sync();
+  int ok = 1;
+  for (int p = 0; p < r; ++p) {
+    const df pv = W[p * r + p].re;
+    if (!((pv.hi > 1e-30f) && isfinite(pv.hi))) {
+      ok = 0;
+      break;
+    }
+    const df ip = df_rcp(pv);
+    for (int e = t; e < 2 * r; e += nt) {
+      if (e < r) {
+        colp[e] = W[e * r + p];
+      } else {
+        const int j = e - r;
+        rowp[j] = (j == p) ? dfc{ip, df{0.f, 0.f}} : dfc_scale(W[p * r + j], ip);
+      }
+    }
+    sync();
+    const df nip = df_neg(ip);
+    for (int e = t; e < r * r; e += nt) {
+      const int i = e / r, j = e - i * r;
+      dfc v;
+      if (i == p) v = rowp[j];
+      else if (j == p) v = dfc_scale(colp[i], nip);
+      else v = dfc_sub(W[e], dfc_mul(colp[i], rowp[j]));
+      W[e] = v;
+    }
+    sync();
+  }
+  for (int e = t; e < r * r; e += nt) {
+    const dfc v = W[e];
+    W64[e] = cx<double>{df_to(v.re), df_to(v.im)};
+  }
+  sync();
+  return ok;
 }
 
 // Gauss-Jordan inverse of the Hermitian r x r matrix A (r <= RP <= 16) by one
@@ -143,7 +246,8 @@ __device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in)
   return 1;
 }
 
-template <typename T, int RP>
+// DF: the block inverse (r > 16) of an FP64 matrix runs in df64 arithmetic.
+template <typename T, int RP, bool DF = false>
 __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
                                       int r, T rtol, bool force_eig = false) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -154,7 +258,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
     __syncthreads();
     return 0;
   }
-  if constexpr (RP <= 16) {
+  if constexpr (RP <= 16 && !DF) {
     // W receives A^-1 (row-major r x r)
     if (tid < 32) {
       T an, in;
@@ -176,30 +280,29 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
       return 1;
     }
   } else {
-    const int n2c = 2 * r;  // augmented columns [A | I], row-major r x 2r
-    for (int e = tid; e < r * n2c; e += nt) {
-      const int i = e / n2c, j = e - i * n2c;
-      W[e] = (j < r) ? A[i * r + j] : cx<T>{(j - r == i) ? T(1) : T(0), T(0)};
-    }
+    for (int e = tid; e < r * r; e += nt) W[e] = A[e];
     if (tid < 32) {
-      const T an = warp_norm1_bound(A, r, 0, r);
+      const T an = warp_frob(A, r, 0, r);
       if (tid == 0) sred[0] = an;
     }
     __syncthreads();
     const T anorm = sred[0];
     ok = (anorm > T(0)) && isfinite(anorm);
-    if (ok) ok = gauss_jordan<T>(W, piv, r, tid, nt, []() { __syncthreads(); });
+    if (ok) {
+      if constexpr (DF && sizeof(T) == 8) ok = gauss_jordan_inplace_df(W, piv, r, tid, nt, []() { __syncthreads(); });
+      else ok = gauss_jordan_inplace<T>(W, piv, r, tid, nt, []() { __syncthreads(); });
+    }
     if (tid < 32) {
-      const T in = ok ? warp_norm1_bound(W, n2c, r, r) : T(0);
-      if (tid == 0) sred[1] = (ok && isfinite(in) && anorm * in < T(0.1) / rtol) ? T(1) : T(0);
+      const T in = ok ? warp_frob(W, r, 0, r) : T(0);
+      if (tid == 0) sred[1] = (ok && isfinite(in) && anorm * in < T(0.5) / rtol) ? T(1) : T(0);
     }
     __syncthreads();
     ok = sred[1] != T(0);
     if (ok) {
       for (int e = tid; e < r * r; e += nt) {
         const int i = e / r, j = e - i * r;
-        const cx<T> a = W[i * n2c + r + j];
-        const cx<T> b = W[j * n2c + r + i];
+        const cx<T> a = W[i * r + j];
+        const cx<T> b = W[j * r + i];
         Ap[e] = cx<T>{T(0.5) * (a.re + b.re), T(0.5) * (a.im - b.im)};
         P[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
       }
@@ -490,16 +593,23 @@ __device__ __forceinline__ void block_max_to(double v, unsigned long long* dst) 
 }
 
 struct XLayout {
-  size_t mats, ht, xs, qs, ts, total;
+  size_t mats, ht, gs, xs, qs, ts, total;
 };
 
-template <typename T>
+// Rows of X~' and X~ staged per step of the X-step Grams; rows are padded to
+// kGramLd complex values (odd, so the threads of a warp that read different
+// columns hit different banks).
+constexpr int kGramRows = 32;
+constexpr int kGramLd = kGramRows + 1;
+
+// TS: the type of the r x r solves (the pseudo-inverses); T: everything else.
+template <typename T, typename TS = T>
 __host__ __device__ inline XLayout xstep_layout(int n1, int n2, int r, bool arrays_in_smem) {
   XLayout L{};
   const size_t rr = (size_t)r * r;
   size_t off = 0;
   L.mats = off;  // A, A^+, P, V, work (2), G, Dg, pivots, reductions
-  off = align_up(off + (rr * 8 + 3 * (size_t)r + 2) * sizeof(cx<T>), 16);
+  off = align_up(off + (rr * 8 + 3 * (size_t)r + 2) * sizeof(cx<TS>), 16);
   L.ht = off;
   off = align_up(off + sizeof(T) * 2 * n1, 16);
   if (arrays_in_smem) {
@@ -509,6 +619,14 @@ __host__ __device__ inline XLayout xstep_layout(int n1, int n2, int r, bool arra
     off = align_up(off + sizeof(cx<T>) * r * n1, 16);
     L.ts = off;
     off = align_up(off + sizeof(cx<T>) * r * n1, 16);
+  }
+  // Gram staging rows: in the Q array when it is in shared memory and large
+  // enough (Q is dead once B is formed), else a region of their own
+  if (arrays_in_smem && n1 >= 2 * kGramLd) {
+    L.gs = L.qs;
+  } else {
+    L.gs = off;
+    off = align_up(off + sizeof(cx<T>) * 2 * (size_t)r * kGramLd, 16);
   }
   L.total = off;
   return L;
@@ -593,23 +711,35 @@ __device__ __forceinline__ cx<T> hth_at(const cx<T>* x, int i, int n1) {
   return v;
 }
 
-template <typename T, int RP>
-__global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
+template <typename T, typename S>
+__device__ __forceinline__ cx<T> cvt(cx<S> v) {
+  return cx<T>{(T)v.re, (T)v.im};
+}
+
+// TS is the type of the two r x r pseudo-inverses (double in the precision
+// form, where the Grams go to FP64 for the solve); the contractions run in T.
+// Threads of the X-step CTA: 1024 for r > 16, where one CTA per slice does
+// r^3 solve steps and r^2 n1 Gram products (more warps hide the latencies and
+// the Gauss-Jordan steps take one element per thread).
+__host__ __device__ constexpr int xstep_threads(int rp) { return rp > 16 ? 1024 : kSliceThreads; }
+
+template <typename T, int RP, typename TS = T>
+__global__ void __launch_bounds__(xstep_threads(RP)) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (converged(d)) return;
   const int k = blockIdx.x;
   const int n1 = d.n1, n2 = d.n2, r = d.r, rr = r * r;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const XLayout lay = xstep_layout<T>(n1, n2, r, arrays_in_smem != 0);
-  cx<T>* A = reinterpret_cast<cx<T>*>(smem + lay.mats);
-  cx<T>* Ap = A + rr;
-  cx<T>* P = Ap + rr;
-  cx<T>* V = P + rr;
-  cx<T>* Wk = V + rr;
-  cx<T>* Gm = Wk + 2 * rr;
-  cx<T>* Dgm = Gm + rr;
-  cx<T>* pivbuf = Dgm + rr;  // 3 r
-  T* sred = reinterpret_cast<T*>(pivbuf + 3 * r);
+  const XLayout lay = xstep_layout<T, TS>(n1, n2, r, arrays_in_smem != 0);
+  cx<TS>* A = reinterpret_cast<cx<TS>*>(smem + lay.mats);
+  cx<TS>* Ap = A + rr;
+  cx<TS>* P = Ap + rr;
+  cx<TS>* V = P + rr;
+  cx<TS>* Wk = V + rr;
+  cx<TS>* Gm = Wk + 2 * rr;
+  cx<TS>* Dgm = Gm + rr;
+  cx<TS>* pivbuf = Dgm + rr;  // 3 r
+  TS* sred = reinterpret_cast<TS*>(pivbuf + 3 * r);
   T* hinv = reinterpret_cast<T*>(smem + lay.ht);
   T* ha = hinv + n1;
   cx<T>* Xs;
@@ -633,7 +763,7 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
   for (int i = tid; i < 2 * n1; i += blockDim.x) hinv[i] = d.hinv[i];
   const bool realslice = (k == 0) || (2 * k == d.n3);
   const T rho1 = d.rho1;
-  const T rtol = (T)d.rtol;
+  const TS rtol = (TS)d.rtol;
 
   // ---- A = Y~Y~^H: FP64 sums of the 32-column tile Grams written by k_ystep ----------
   {
@@ -651,30 +781,56 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
       for (; t < d.ytiles; ++t) acc[0] = acc[0] + ag[(size_t)t * ntask + task];
       cx<double> v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
       if (s == u) v.im = 0.0;
-      A[s * r + u] = cx<T>{(T)v.re, (T)v.im};
-      A[u * r + s] = cx<T>{(T)v.re, (T)(-v.im)};
+      A[s * r + u] = cx<TS>{(TS)v.re, (TS)v.im};
+      A[u * r + s] = cx<TS>{(TS)v.re, (TS)(-v.im)};
     }
   }
   __syncthreads();
-  const bool certA = block_pinv_herm<T, RP>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0) != 0;
+  constexpr bool kDF = sizeof(T) == 4 && sizeof(TS) == 8;  // FP64 solves of an FP32 engine: df64
+  const bool certA = block_pinv_herm<TS, RP, kDF>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0) != 0;
   // step along d_X: 1, or alpha / L1 with L1 = ||H_rho1||_2 lambda_max(A)
-  const T t1 = d.scaled ? ((sred[2] > T(0)) ? d.alpha / (d.hnorm * sred[2]) : T(0)) : T(1);
+  const T t1 = d.scaled ? ((sred[2] > TS(0)) ? d.alpha / (d.hnorm * (T)sred[2]) : T(0)) : T(1);
 
   // ---- B = Q A^+ - rho1 (H^T H X~) P ------------------------------------------------------
-  for (int e = tid; e < r * n1; e += blockDim.x) {
-    const int s = e / n1, i = e - s * n1;
-    cx<T> acc = {T(0), T(0)};
-    for (int u = 0; u < r; ++u) cfma(acc, Qs[(size_t)u * n1 + i], Ap[u * r + s]);
-    if (rho1 != T(0)) {
-      cx<T> hx = {T(0), T(0)};
-      if (certA) {
-        hx = hth_at(Xs + (size_t)s * n1, i, n1);  // P = I
-      } else {
-        for (int u = 0; u < r; ++u) cfma(hx, hth_at(Xs + (size_t)u * n1, i, n1), P[u * r + s]);
+  // A^+ and P in T (the work area of the solve is free again); a thread forms
+  // SB columns of one row, so each Q value it loads feeds SB products.
+  cx<T>* ApT = reinterpret_cast<cx<T>*>(Wk);
+  cx<T>* PT = ApT + rr;
+  for (int e = tid; e < rr; e += blockDim.x) {
+    ApT[e] = cvt<T>(Ap[e]);
+    PT[e] = cvt<T>(P[e]);
+  }
+  __syncthreads();
+  {
+    constexpr int SB = RP < 8 ? RP : 8;
+    const int nsb = (r + SB - 1) / SB;
+    for (int e = tid; e < nsb * n1; e += blockDim.x) {
+      const int sb = e / n1, i = e - sb * n1, s0 = sb * SB;
+      cx<T> acc[SB];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) acc[c] = cx<T>{T(0), T(0)};
+      for (int u = 0; u < r; ++u) {
+        const cx<T> q = Qs[(size_t)u * n1 + i];
+#pragma unroll
+        for (int c = 0; c < SB; ++c)
+          if (s0 + c < r) cfma(acc[c], q, ApT[u * r + s0 + c]);
       }
-      acc = acc - hx * rho1;
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        const int s = s0 + c;
+        if (s >= r) break;
+        if (rho1 != T(0)) {
+          cx<T> hx = {T(0), T(0)};
+          if (certA) {
+            hx = hth_at(Xs + (size_t)s * n1, i, n1);  // P = I
+          } else {
+            for (int u = 0; u < r; ++u) cfma(hx, hth_at(Xs + (size_t)u * n1, i, n1), PT[u * r + s]);
+          }
+          acc[c] = acc[c] - hx * rho1;
+        }
+        Ts[(size_t)s * n1 + i] = acc[c];
+      }
     }
-    Ts[e] = acc;
   }
   __syncthreads();
   // ---- d_X = H_rho1^{-1} B: one warp per column --------------------------------------------
@@ -697,57 +853,82 @@ __global__ void __launch_bounds__(kSliceThreads) k_xstep(Dev<T> d, const cx<T>* 
   // ---- G = X~'^H H_rho1 X~' (Hermitian) and Dg = E - G ----------------------------------
   // (H X~')^H (H X~') = sum_i conj(x_i - x_{i+1}) (x_i - x_{i+1}) row by row.
   // tp adjacent threads share one (s, u) pair and split the rows; their partial
-  // sums are combined by shuffles in a fixed order.
+  // sums are combined by shuffles in a fixed order.  The rows go through
+  // shared memory kGramRows at a time (X~' with one row of halo).
   {
     int tp = 1;
     while (tp < 32 && tp * 2 * rr <= (int)blockDim.x) tp *= 2;
     const int per_pass = blockDim.x / tp;
-    for (int base = 0; base < rr; base += per_pass) {
-      const int task = base + tid / tp, q = tid & (tp - 1);
-      const bool has = task < rr;
-      const int s = has ? task / r : 0, u = has ? task - s * r : 0;
-      cx<T> a0 = {T(0), T(0)}, hh = {T(0), T(0)}, dd = {T(0), T(0)};
-      if (has) {
-        const cx<T>* xs = Ts + (size_t)s * n1;
-        const cx<T>* xu = Ts + (size_t)u * n1;
-        const cx<T>* ou = Xs + (size_t)u * n1;
-        for (int i = q; i < n1; i += tp) {
-          const cx<T> a = xs[i], b = xu[i];
-          cfmaconj(a0, a, b);
-          cfmaconj(dd, a, b - ou[i]);
-          if (i + 1 < n1) cfmaconj(hh, a - xs[i + 1], b - xu[i + 1]);
+    const int q = tid & (tp - 1);
+    constexpr int MT = (RP * RP + xstep_threads(RP) - 1) / xstep_threads(RP);  // passes (tp = 1 when r r >= threads)
+    cx<T> a0[MT], hh[MT], dd[MT];
+#pragma unroll
+    for (int t = 0; t < MT; ++t) a0[t] = hh[t] = dd[t] = cx<T>{T(0), T(0)};
+    cx<T>* gx = reinterpret_cast<cx<T>*>(smem + lay.gs);  // [r][kGramLd] rows i0 .. i0 + kGramRows of X~'
+    cx<T>* go = gx + (size_t)r * kGramLd;                 // [r][kGramLd] rows i0 .. of X~
+    for (int i0 = 0; i0 < n1; i0 += kGramRows) {
+      const int nrow = min(kGramRows + 1, n1 - i0);
+      for (int e = tid; e < r * kGramLd; e += blockDim.x) {
+        const int s = e / kGramLd, ii = e - s * kGramLd;
+        if (ii < nrow) {
+          gx[e] = Ts[(size_t)s * n1 + i0 + ii];
+          if (ii < kGramRows) go[e] = Xs[(size_t)s * n1 + i0 + ii];
         }
       }
-      for (int o = tp >> 1; o > 0; o >>= 1) {
-        a0.re += __shfl_xor_sync(0xffffffffu, a0.re, o);
-        a0.im += __shfl_xor_sync(0xffffffffu, a0.im, o);
-        hh.re += __shfl_xor_sync(0xffffffffu, hh.re, o);
-        hh.im += __shfl_xor_sync(0xffffffffu, hh.im, o);
-        dd.re += __shfl_xor_sync(0xffffffffu, dd.re, o);
-        dd.im += __shfl_xor_sync(0xffffffffu, dd.im, o);
+      __syncthreads();
+      const int iend = min(kGramRows, n1 - i0);
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        const int task = t * per_pass + tid / tp;
+        if (task < rr) {
+          const int s = task / r, u = task - s * r;
+          const cx<T>* xs = gx + s * kGramLd;
+          const cx<T>* xu = gx + u * kGramLd;
+          const cx<T>* ou = go + u * kGramLd;
+          for (int ii = q; ii < iend; ii += tp) {
+            const cx<T> a = xs[ii], b = xu[ii];
+            cfmaconj(a0[t], a, b);
+            cfmaconj(dd[t], a, b - ou[ii]);
+            if (i0 + ii + 1 < n1) cfmaconj(hh[t], a - xs[ii + 1], b - xu[ii + 1]);
+          }
+        }
       }
-      if (has && q == 0) {
-        cx<T> dg = {-(dd.re + rho1 * hh.re), -(dd.im + rho1 * hh.im)};
+      __syncthreads();
+    }
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      for (int o = tp >> 1; o > 0; o >>= 1) {
+        a0[t].re += __shfl_xor_sync(0xffffffffu, a0[t].re, o);
+        a0[t].im += __shfl_xor_sync(0xffffffffu, a0[t].im, o);
+        hh[t].re += __shfl_xor_sync(0xffffffffu, hh[t].re, o);
+        hh[t].im += __shfl_xor_sync(0xffffffffu, hh[t].im, o);
+        dd[t].re += __shfl_xor_sync(0xffffffffu, dd[t].re, o);
+        dd[t].im += __shfl_xor_sync(0xffffffffu, dd[t].im, o);
+      }
+      const int task = t * per_pass + tid / tp;
+      if (task < rr && q == 0) {
+        const int s = task / r, u = task - s * r;
+        cx<T> dg = {-(dd[t].re + rho1 * hh[t].re), -(dd[t].im + rho1 * hh[t].im)};
         if (realslice) dg.im = T(0);
-        Dgm[s * r + u] = dg;
+        Dgm[s * r + u] = cvt<TS>(dg);
         if (s <= u) {
-          cx<T> g = {a0.re + rho1 * hh.re, a0.im + rho1 * hh.im};
+          cx<T> g = {a0[t].re + rho1 * hh[t].re, a0[t].im + rho1 * hh[t].im};
           if (s == u || realslice) g.im = T(0);
-          Gm[s * r + u] = g;
-          Gm[u * r + s] = cx<T>{g.re, -g.im};
+          Gm[s * r + u] = cvt<TS>(g);
+          Gm[u * r + s] = cx<TS>{(TS)g.re, -(TS)g.im};
         }
       }
     }
   }
   __syncthreads();
-  block_pinv_herm<T, RP>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0);
+  block_pinv_herm<TS, RP, kDF>(Gm, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0);
   // step along d_Y: 1, or beta / L2 with L2 = lambda_max(G), folded into G^+
-  const T t2 = d.scaled ? ((sred[2] > T(0)) ? d.beta / sred[2] : T(0)) : T(1);
+  const TS t2 = d.scaled ? ((sred[2] > TS(0)) ? (TS)d.beta / sred[2] : TS(0)) : TS(1);
   // ---- Dg and t G^+ for k_ystep; X~ <- X~' -------------------------------------------------
   for (int e = tid; e < rr; e += blockDim.x) {
-    cx<T> gp = Ap[e] * t2;
+    cx<T> gp = cvt<T>(Ap[e] * t2);
     if (realslice) gp.im = T(0);
-    d.Dg[(size_t)k * rr + e] = Dgm[e];
+    d.Dg[(size_t)k * rr + e] = cvt<T>(Dgm[e]);
     d.Gp[(size_t)k * rr + e] = gp;
   }
   for (int e = tid; e < r * n1; e += blockDim.x) Xg[e] = Ts[e];
@@ -767,7 +948,9 @@ constexpr int kYThreads = 256;
 
 __host__ __device__ constexpr int ystep_cpl(int rp) { return rp <= 16 ? 2 : 1; }
 
-template <typename T, int RP>
+// TCY (precision form, r > 16): D comes as ksplit partial sums over ranges of
+// n1 from k_dcon_tc (d.Dpart) and Z~ is formed by k_zsyn_tc afterwards.
+template <typename T, int RP, bool TCY = false>
 __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   constexpr int CPL = ystep_cpl(RP), TW = 32 * CPL;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -777,14 +960,18 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S, rr = r * r;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   cx<T>* red = reinterpret_cast<cx<T>*>(smem);  // [nw][RP][TW]
-  cx<T>* Ds = red + nw * RP * TW;               // [RP][TW]
+  cx<T>* Ds = red + (TCY ? 0 : nw * RP * TW);   // [RP][TW]
   cx<T>* Yo = Ds + RP * TW;                     // [RP][TW]
   cx<T>* Dgs = Yo + RP * TW;                    // [rr]
   cx<T>* Gh = Dgs + rr;                         // [rr]
   cx<T>* Yn = Gh + rr;                          // [RP][TW] the new Y~' of the tile
-  cx<T>* Xs = Yn + RP * TW;                     // [r][n1]
   const cx<T>* Xg = d.Xt + (size_t)k * r * n1;
-  for (int e = tid; e < r * n1; e += blockDim.x) Xs[e] = Xg[e];
+  const cx<T>* Xs = Xg;                         // [r][n1], staged when it fits
+  if (!TCY && !d.yx_global) {
+    cx<T>* xs = Yn + RP * TW;
+    for (int e = tid; e < r * n1; e += blockDim.x) xs[e] = Xg[e];
+    Xs = xs;
+  }
   for (int e = tid; e < rr; e += blockDim.x) {
     Dgs[e] = d.Dg[(size_t)k * rr + e];
     Gh[e] = d.Gp[(size_t)k * rr + e];
@@ -804,7 +991,7 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   for (int h = 0; h < CPL; ++h) live[h] = j0 + 32 * h + lane < n2;
   const cx<T>* rbase = d.Rt + (size_t)k * n2 + j0 + lane;  // + i * S * n2 + 32 h
   const size_t rstride = (size_t)S * n2;
-  {
+  if constexpr (!TCY) {
     int i = wid;
     for (; i + nw < n1; i += 2 * nw) {
       cx<T> v[2][CPL];
@@ -837,16 +1024,23 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
         }
     }
   }
+  if constexpr (!TCY) {
 #pragma unroll
-  for (int s = 0; s < RP; ++s)
+    for (int s = 0; s < RP; ++s)
 #pragma unroll
-    for (int h = 0; h < CPL; ++h) red[(wid * RP + s) * TW + 32 * h + lane] = acc[h][s];
+      for (int h = 0; h < CPL; ++h) red[(wid * RP + s) * TW + 32 * h + lane] = acc[h][s];
+  }
   __syncthreads();
   // V = Dg Y~ + D (= -grad_Y on the tile)
   for (int e = tid; e < r * TW; e += blockDim.x) {
     const int s = e / TW, c = e - s * TW;
     cx<T> v = {T(0), T(0)};
-    for (int w = 0; w < nw; ++w) v = v + red[(w * RP + s) * TW + c];
+    if constexpr (TCY) {
+      if (j0 + c < n2)
+        for (int z = 0; z < d.ksplit; ++z) v = v + d.Dpart[(((size_t)k * d.ksplit + z) * r + s) * n2 + j0 + c];
+    } else {
+      for (int w = 0; w < nw; ++w) v = v + red[(w * RP + s) * TW + c];
+    }
     for (int u = 0; u < r; ++u) cfma(v, Dgs[s * r + u], Yo[u * TW + c]);
     Ds[s * TW + c] = v;
   }
@@ -885,6 +1079,7 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   }
 
   // ---- Z~(:, tile, k) = X~' Y~'  (step 3, written for the slab kernel) ----------------
+  if constexpr (TCY) return;
   cx<T> yv[CPL][RP];
 #pragma unroll
   for (int h = 0; h < CPL; ++h)
@@ -913,9 +1108,11 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
 }
 
 template <typename T>
-__host__ inline size_t ystep_smem_bytes(int n1, int r, int rp) {
+__host__ inline size_t ystep_smem_bytes(int n1, int r, int rp, bool x_in_smem = true, bool tcy = false) {
   const size_t tw = 32 * (size_t)ystep_cpl(rp);
-  return ((size_t)(kYThreads / 32 + 3) * rp * tw + 2 * (size_t)r * r + (size_t)r * n1) * sizeof(cx<T>);
+  return ((size_t)((tcy ? 0 : kYThreads / 32) + 3) * rp * tw + 2 * (size_t)r * r +
+          (x_in_smem && !tcy ? (size_t)r * n1 : 0)) *
+         sizeof(cx<T>);
 }
 
 template <typename T>

@@ -1,9 +1,11 @@
 // C ABI of the TCTF2R library (declared in include/tctf2r.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tc_engine.h"
 #include "tctf2r.h"
@@ -34,12 +36,11 @@ tc_status validate(const tc_params* p) {
   if (!(p->mu >= 0) || !(p->rho1 >= 0) || !(p->rho2 >= 0) || !std::isfinite(p->mu) || !std::isfinite(p->rho1) ||
       !std::isfinite(p->rho2))
     return fail(TC_ERR_ARG, "mu, rho1, rho2 must be finite and >= 0");
-  if (p->flags != 0) return fail(TC_ERR_ARG, "flags must be 0");
-  if (p->precision != TC_FP64 && p->precision != TC_FP32) {
-    if (p->precision == TC_TF32 || p->precision == TC_BF16)
-      return fail(TC_ERR_UNSUPPORTED, "TF32/BF16 precision is not built");
+  if (p->precision != TC_FP64 && p->precision != TC_FP32 && p->precision != TC_TF32 && p->precision != TC_BF16)
     return fail(TC_ERR_ARG, "unknown precision");
-  }
+  const bool mixed = p->precision == TC_TF32 || p->precision == TC_BF16;
+  if ((p->flags & ~(int32_t)TC_FLAG_SINGLE_PASS) != 0 || (!mixed && p->flags != 0))
+    return fail(TC_ERR_ARG, "unknown flags, or TC_FLAG_SINGLE_PASS without TC_TF32 / TC_BF16");
   if (p->step != TC_STEP_EXACT && p->step != TC_STEP_SCALED) return fail(TC_ERR_ARG, "unknown step rule");
   if (p->step == TC_STEP_SCALED &&
       (!(p->alpha > 0) || !(p->beta > 0) || !std::isfinite(p->alpha) || !std::isfinite(p->beta)))
@@ -158,6 +159,193 @@ tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* 
   if (stopped) *stopped = s;
   if (iters_run) *iters_run = it;
   return st == TC_OK ? st : fail(st, err);
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many contexts advanced by one CUDA graph per iteration.  The
+// graph holds one child graph per instance (its captured iteration) in K
+// independent chains; instance i runs in chain i mod K, so independent
+// completions of different sizes fill the GPU together.  The
+// first iterations try each candidate K once or twice (each trial is a real
+// iteration of every instance, so the results do not depend on the choice)
+// and keep the fastest.
+// ---------------------------------------------------------------------------
+struct tc_batch {
+  std::vector<tc_ctx*> ctxs;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<int> cand;              // branch counts of the candidate graphs
+  std::vector<cudaGraphExec_t> exec;  // one per candidate
+  std::vector<float> best_ms;         // best trial time per candidate
+  std::vector<int> trials;
+  int chosen = -1;
+  std::vector<cudaGraph_t> child;     // one captured iteration per instance
+  std::vector<cudaEvent_t> ctx_ev;
+  cudaEvent_t t0 = nullptr, t1 = nullptr, done = nullptr;
+
+  void release() {
+    for (auto e : exec)
+      if (e) cudaGraphExecDestroy(e);
+    for (auto g : child)
+      if (g) cudaGraphDestroy(g);
+    for (auto e : ctx_ev)
+      if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {t0, t1, done})
+      if (e) cudaEventDestroy(e);
+    exec.clear();
+    child.clear();
+    ctx_ev.clear();
+    t0 = t1 = done = nullptr;
+  }
+};
+
+namespace {
+
+constexpr int kBatchTrials = 2;
+
+// The batched graph: one child graph per instance (its own captured
+// iteration), chained K ways; chain j runs instances j, j + K, ...
+tc_status batch_build(tc_batch* b, int K, cudaGraphExec_t* out, std::string& err) {
+  cudaGraph_t parent = nullptr;
+  cudaError_t e = cudaGraphCreate(&parent, 0);
+  std::vector<cudaGraphNode_t> last(K, nullptr);
+  for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i) {
+    const int j = (int)(i % K);
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddChildGraphNode(&node, parent, last[j] ? &last[j] : nullptr, last[j] ? 1 : 0, b->child[i]);
+    last[j] = node;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, parent, 0);
+  if (parent) cudaGraphDestroy(parent);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    err = std::string("batched graph build failed: ") + cudaGetErrorString(e);
+    return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
+}  // namespace
+
+tc_status tc_batch_create(tc_batch** out, tc_ctx* const* ctxs, int32_t count, void* cuda_stream) {
+  g_last_error.clear();
+  if (!out) return fail(TC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || count < 1) return fail(TC_ERR_ARG, "ctxs must hold count >= 1 contexts");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return fail(TC_ERR_ARG, "a context is NULL");
+    if (ctxs[i]->device != dev) return fail(TC_ERR_ARG, "all contexts must live on the current device");
+    if (ctxs[i]->eng->poisoned()) return fail(TC_ERR_STATE, "a context is poisoned by an earlier error");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(TC_ERR_ARG, "a context appears twice");
+  }
+  tc_batch* b = new (std::nothrow) tc_batch();
+  if (!b) return fail(TC_ERR_NOMEM, "host allocation failed");
+  b->ctxs.assign(ctxs, ctxs + count);
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->device = dev;
+  for (int K : {1, 4, 16, count})
+    if (K <= count && std::find(b->cand.begin(), b->cand.end(), K) == b->cand.end()) b->cand.push_back(K);
+  std::string err;
+  cudaError_t e = cudaSuccess;
+  b->ctx_ev.assign(count, nullptr);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ctx_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+  if (e != cudaSuccess) {
+    b->release();
+    delete b;
+    return fail(TC_ERR_CUDA, std::string("batch set-up failed: ") + cudaGetErrorString(e));
+  }
+  b->child.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    tc_status st = b->ctxs[i]->eng->capture_iteration(&b->child[i], err);
+    if (st != TC_OK) {
+      b->release();
+      delete b;
+      return fail(st, err);
+    }
+  }
+  b->exec.assign(b->cand.size(), nullptr);
+  for (size_t c = 0; c < b->cand.size(); ++c) {
+    tc_status st = batch_build(b, b->cand[c], &b->exec[c], err);
+    if (st != TC_OK) {
+      b->release();
+      delete b;
+      return fail(st, err);
+    }
+  }
+  b->best_ms.assign(b->cand.size(), 1e30f);
+  b->trials.assign(b->cand.size(), 0);
+  if (b->cand.size() == 1) b->chosen = 0;
+  *out = b;
+  return TC_OK;
+}
+
+tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters) {
+  g_last_error.clear();
+  if (!b) return fail(TC_ERR_ARG, "batch is NULL");
+  if (n_iters < 0) return fail(TC_ERR_ARG, "n_iters must be >= 0");
+  if (n_iters == 0) return TC_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  cudaError_t e = cudaSuccess;
+  // after the work already queued on every context's stream
+  for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(b->ctx_ev[i], b->ctxs[i]->eng->stream());
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ctx_ev[i], 0);
+  }
+  for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
+    if (b->chosen < 0) {
+      // tuning: the candidate with the fewest trials, timed on its own
+      size_t c = 0;
+      for (size_t q = 1; q < b->cand.size(); ++q)
+        if (b->trials[q] < b->trials[c]) c = q;
+      e = cudaEventRecord(b->t0, b->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[c], b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->t0, b->t1);
+      if (e != cudaSuccess) break;
+      b->best_ms[c] = std::min(b->best_ms[c], ms);
+      if (++b->trials[c] >= kBatchTrials &&
+          *std::min_element(b->trials.begin(), b->trials.end()) >= kBatchTrials)
+        b->chosen = (int)(std::min_element(b->best_ms.begin(), b->best_ms.end()) - b->best_ms.begin());
+    } else {
+      e = cudaGraphLaunch(b->exec[b->chosen], b->stream);
+    }
+  }
+  // every context's later calls come after the batch
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
+  for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(b->ctxs[i]->eng->stream(), b->done, 0);
+  if (prev != b->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("batched iteration failed: ") + cudaGetErrorString(e));
+  return TC_OK;
+}
+
+tc_status tc_batch_branches(tc_batch* b, int32_t* branches) {
+  g_last_error.clear();
+  if (!b || !branches) return fail(TC_ERR_ARG, "batch and branches are required");
+  *branches = (b->chosen < 0) ? 0 : b->cand[b->chosen];
+  return TC_OK;
+}
+
+tc_status tc_batch_free(tc_batch* b) {
+  if (!b) return TC_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != b->device) cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  b->release();
+  if (prev != b->device) cudaSetDevice(prev);
+  delete b;
+  return TC_OK;
 }
 
 tc_status tc_free(tc_ctx* c) {

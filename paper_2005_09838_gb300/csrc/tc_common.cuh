@@ -4,7 +4,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 namespace tc {
+
+// The dynamic shared-memory limit is an attribute of the kernel itself, shared
+// by every live context that launches it: raise it to `bytes` if it is lower,
+// never lower it (a smaller context created later must not break the launches
+// of a larger one).
+inline cudaError_t allow_dynamic_smem(const void* f, size_t bytes) {
+  static std::mutex m;
+  std::lock_guard<std::mutex> g(m);
+  cudaFuncAttributes a{};
+  cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 // Complex value in (re, im) order; layout-compatible with float2 / double2.
 template <typename T>
@@ -84,6 +100,7 @@ enum DevErr : int {
   DEV_BAD_LAUNCH = 1,   // launch shape does not match the sizes
   DEV_BAD_SIZE = 2,     // size outside what a kernel instance supports
   DEV_NONFINITE = 3,    // a non-finite value where a finite one is required
+  DEV_TIMEOUT = 4,      // a bounded wait on the tensor core gave up
 };
 
 __device__ __forceinline__ void set_err(int* err, int code) {

@@ -82,16 +82,61 @@ inline YFn<T> pick_ystep(int rp) {
 template <typename T>
 using XFn = void (*)(Dev<T>, const cx<T>*, int);
 
+// Type of the r x r solves: FP64 storage (df64 arithmetic, see
+// gauss_jordan_inplace_df) in an FP32 engine for r > 16, whose Grams (the DC
+// slice above all) are too ill-conditioned for an FP32 inverse, and for every
+// r in the precision form; the working precision otherwise.
 template <typename T>
+inline bool solve64(int rp, bool mixed) {
+  return sizeof(T) == 4 && (mixed || rp == 32);
+}
+
+// Default cutoff of the pseudo-inverse: r times the epsilon of the solve type.
+template <typename T>
+inline double default_rtol(int r, int rp, bool mixed) {
+  return (double)r * (solve64<T>(rp, mixed) ? std::numeric_limits<double>::epsilon()
+                                             : (double)std::numeric_limits<T>::epsilon());
+}
+
+template <typename T>
+inline XLayout xstep_layout_for(int n1, int n2, int r, int rp, bool mixed, bool in_smem) {
+  return solve64<T>(rp, mixed) ? xstep_layout<T, double>(n1, n2, r, in_smem) : xstep_layout<T>(n1, n2, r, in_smem);
+}
+
+template <typename T, typename TS = T>
 inline XFn<T> pick_xstep(int rp) {
   switch (rp) {
-    case 2: return k_xstep<T, 2>;
-    case 4: return k_xstep<T, 4>;
-    case 8: return k_xstep<T, 8>;
-    case 16: return k_xstep<T, 16>;
-    default: return k_xstep<T, 32>;
+    case 2: return k_xstep<T, 2, TS>;
+    case 4: return k_xstep<T, 4, TS>;
+    case 8: return k_xstep<T, 8, TS>;
+    case 16: return k_xstep<T, 16, TS>;
+    default: return k_xstep<T, 32, TS>;
   }
 }
+
+// Tensor-core Q contraction of the precision form (TC_TF32 / TC_BF16 over
+// FP32 data, r > 16): the kernel and its dynamic shared memory, or nullptr
+// where it is not built (FP64 data).
+template <typename T>
+inline XFn<T> pick_xstep_for(int rp, bool mixed) {
+  return solve64<T>(rp, mixed) ? pick_xstep<T, double>(rp) : pick_xstep<T>(rp);
+}
+
+// Tensor-core kernels of the precision form (TC_TF32 / TC_BF16 over FP32
+// data, r > 16): Q contraction, partial D of the Y-step, Z~ synthesis, with
+// their dynamic shared memory.  False where they are not built (FP64 data).
+template <typename T>
+struct TcKernels {
+  QFn<T> qcon = nullptr;
+  YFn<T> dcon = nullptr, zsyn = nullptr;
+  size_t qsm = 0, dsm = 0, zsm = 0;
+};
+template <typename T>
+bool pick_tc(int precision, bool split, TcKernels<T>& k);
+template <>
+bool pick_tc<float>(int precision, bool split, TcKernels<float>& k);
+template <>
+bool pick_tc<double>(int precision, bool split, TcKernels<double>& k);
 
 template <typename T>
 inline QFn<T> pick_qcon(int rp) {
@@ -194,28 +239,59 @@ class Engine final : public EngineBase {
       slab_smem_ = lay.total;
     }
     for (int m = 0; m < 3; ++m)
-      TC_CUDA_TRY(cudaFuncSetAttribute(slab_[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)slab_[m], slab_smem_));
 
-    XLayout xl = xstep_layout<T>(n1_, n2_, r_, true);
+    // precision form: r x r solves in FP64, contractions on the tensor cores for r > 16
+    mixed_ = p.precision == TC_TF32 || p.precision == TC_BF16;
+    auto xlay = [&](bool in_smem) { return xstep_layout_for<T>(n1_, n2_, r_, rp_, mixed_, in_smem); };
+    XLayout xl = xlay(true);
     xarrays_in_smem_ = xl.total <= (size_t)optin;
-    if (!xarrays_in_smem_) xl = xstep_layout<T>(n1_, n2_, r_, false);
+    if (!xarrays_in_smem_) xl = xlay(false);
     xstep_smem_ = xl.total;
     if (xstep_smem_ > (size_t)optin) {
       err = "X-step shared memory exceeds the device limit";
       return TC_ERR_UNSUPPORTED;
     }
-    xstep_ = pick_xstep<T>(rp_);
-    TC_CUDA_TRY(cudaFuncSetAttribute(xstep_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xstep_smem_));
+    xstep_ = pick_xstep_for<T>(rp_, mixed_);
+    TC_CUDA_TRY(allow_dynamic_smem((const void*)xstep_, xstep_smem_));
     ystep_ = pick_ystep<T>(rp_);
     ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
+    d_.yx_global = ystep_smem_ > (size_t)optin ? 1 : 0;
+    if (d_.yx_global) ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_, false);
     qcon_ = pick_qcon<T>(rp_);
     qcon_smem_ = qcon_smem_bytes<T>(n2_, r_, rp_);
+    qgrid_ = dim3(S_, (n1_ + 31) / 32);
+    qthreads_ = kSliceThreads;
+    if (mixed_ && rp_ == 32 && pick_tc<T>(p.precision, (p.flags & TC_FLAG_SINGLE_PASS) == 0, tck_)) {
+      tcy_ = true;
+      qcon_ = tck_.qcon;
+      qcon_smem_ = tck_.qsm;
+      qgrid_ = dim3(S_, (n1_ + 127) / 128);
+      qthreads_ = 256;
+      ystep_ = k_ystep<T, 32, true>;
+      ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_, false, true);
+      // split the n1 reduction of D so that the grid covers the SMs about twice
+      int nsm = 0;
+      TC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device_));
+      const int ntj = (n2_ + 127) / 128;
+      ksplit_ = std::max(1, std::min((2 * nsm + S_ * ntj - 1) / (S_ * ntj), (n1_ + 31) / 32));
+      d_.ksplit = ksplit_;
+      Dpart_ = alloc<cx<T>>((size_t)S_ * ksplit_ * r_ * n2_, err);
+      if (!err.empty()) return TC_ERR_NOMEM;
+      d_.Dpart = Dpart_;
+      if (tck_.dsm > (size_t)optin || tck_.zsm > (size_t)optin) {
+        err = "shared memory of the tensor-core kernels exceeds the device limit";
+        return TC_ERR_UNSUPPORTED;
+      }
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)tck_.dcon, tck_.dsm));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)tck_.zsyn, tck_.zsm));
+    }
     if (ystep_smem_ > (size_t)optin || qcon_smem_ > (size_t)optin) {
       err = "shared memory of the slice kernels exceeds the device limit for these sizes";
       return TC_ERR_UNSUPPORTED;
     }
-    TC_CUDA_TRY(cudaFuncSetAttribute(ystep_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ystep_smem_));
-    TC_CUDA_TRY(cudaFuncSetAttribute(qcon_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qcon_smem_));
+    TC_CUDA_TRY(allow_dynamic_smem((const void*)ystep_, ystep_smem_));
+    TC_CUDA_TRY(allow_dynamic_smem((const void*)qcon_, qcon_smem_));
 
     // ---- host tables (FP64, rounded to T) ----------------------------------------------
     {
@@ -270,7 +346,7 @@ class Engine final : public EngineBase {
     d_.part = part;
     d_.part_k = part_k;
     d_.err = derr;
-    d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * (double)std::numeric_limits<T>::epsilon();
+    d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : default_rtol<T>(r_, rp_, mixed_);
     d_.scaled = (p.step == TC_STEP_SCALED) ? 1 : 0;
     d_.alpha = (T)p.alpha;
     d_.beta = (T)p.beta;
@@ -461,6 +537,52 @@ class Engine final : public EngineBase {
     return check_dev_err(err);
   }
 
+  tc_status capture_iteration(cudaGraph_t* out, std::string& err) override {
+    if (!cap_stream_) TC_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+    *out = nullptr;
+    const cudaError_t pre = cudaGetLastError();  // an error left by an earlier call of this thread
+    if (pre != cudaSuccess) {
+      err = std::string("pending error before graph capture: ") + cudaGetErrorString(pre);
+      return TC_ERR_CUDA;
+    }
+    TC_CUDA_TRY(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
+    const char* at = "qcon";
+    launch_qcon(cap_stream_);
+    cudaError_t le = cudaPeekAtLastError();
+    if (le == cudaSuccess) {
+      at = "xstep";
+      launch_xstep(cap_stream_);
+      le = cudaPeekAtLastError();
+    }
+    if (le == cudaSuccess) {
+      at = "ystep";
+      launch_ystep(cap_stream_);
+      le = cudaPeekAtLastError();
+    }
+    if (le == cudaSuccess) {
+      at = "slab";
+      launch_slab(MODE_ITER, nullptr, 0, cap_stream_);
+      le = cudaPeekAtLastError();
+    }
+    if (le == cudaSuccess && d_.conv) {
+      at = "check";
+      k_check<T><<<1, 32, 0, cap_stream_>>>(d_);
+      le = cudaPeekAtLastError();
+    }
+    cudaGetLastError();
+    cudaError_t ce = cudaStreamEndCapture(cap_stream_, out);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+      if (*out) cudaGraphDestroy(*out);
+      *out = nullptr;
+      err = std::string("graph capture failed (") + at + "): " + cudaGetErrorString(le != cudaSuccess ? le : ce);
+      poisoned_ = true;
+      return TC_ERR_CUDA;
+    }
+    return TC_OK;
+  }
+  cudaStream_t stream() const override { return stream_; }
+  bool poisoned() const override { return poisoned_; }
+
   tc_status profile(int n, double* ms, std::string& err) override {
     if (poisoned_) {
       err = "context poisoned by an earlier error";
@@ -517,17 +639,16 @@ class Engine final : public EngineBase {
   void launch_slab(int mode, T* Wout, int init, cudaStream_t s) {
     slab_[mode]<<<n1_, slab_threads_, slab_smem_, s>>>(d_, Wout, slabs_in_smem_ ? 1 : 0, init);
   }
-  void launch_qcon(cudaStream_t s) {
-    dim3 g(S_, (n1_ + 31) / 32);
-    qcon_<<<g, kSliceThreads, qcon_smem_, s>>>(d_, Q_);
-  }
+  void launch_qcon(cudaStream_t s) { qcon_<<<qgrid_, qthreads_, qcon_smem_, s>>>(d_, Q_); }
   void launch_xstep(cudaStream_t s) {
-    xstep_<<<S_, kSliceThreads, xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
+    xstep_<<<S_, xstep_threads(rp_), xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
   }
   void launch_ystep(cudaStream_t s) {
     const int tw = 32 * ystep_cpl(rp_);
     dim3 g(S_, (n2_ + tw - 1) / tw);
+    if (tcy_) tck_.dcon<<<dim3(S_, (n2_ + 127) / 128, ksplit_), 256, tck_.dsm, s>>>(d_);
     ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
+    if (tcy_) tck_.zsyn<<<dim3(S_, (n1_ + 127) / 128, (n2_ + 63) / 64), 256, tck_.zsm, s>>>(d_);
   }
 
   // One TCTF2R iteration: Q = R~Y~^H, X-step (+ Y-step r x r work), Y-step,
@@ -547,18 +668,9 @@ class Engine final : public EngineBase {
   }
 
   tc_status capture(std::string& err) {
-    if (!cap_stream_) TC_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
-    TC_CUDA_TRY(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
-    launch_iteration(cap_stream_);
-    cudaError_t le = cudaGetLastError();
-    cudaError_t ce = cudaStreamEndCapture(cap_stream_, &g);
-    if (le != cudaSuccess || ce != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      err = std::string("graph capture failed: ") + cudaGetErrorString(le != cudaSuccess ? le : ce);
-      poisoned_ = true;
-      return TC_ERR_CUDA;
-    }
+    tc_status st = capture_iteration(&g, err);
+    if (st != TC_OK) return st;
     cudaError_t ie = cudaGraphInstantiate(&graph_exec_, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) {
@@ -591,6 +703,13 @@ class Engine final : public EngineBase {
   bool specialised_ = false;
   bool slabs_in_smem_ = true;
   bool xarrays_in_smem_ = true;
+  bool mixed_ = false;
+  bool tcy_ = false;  // tensor-core Y-step (D partials, update, Z~ synthesis)
+  TcKernels<T> tck_;
+  int ksplit_ = 1;
+  cx<T>* Dpart_ = nullptr;
+  dim3 qgrid_;
+  int qthreads_ = kSliceThreads;
   int slab_threads_ = 256;
   size_t slab_smem_ = 0, xstep_smem_ = 0, ystep_smem_ = 0, qcon_smem_ = 0;
   SlabFn<T> slab_[3] = {nullptr, nullptr, nullptr};

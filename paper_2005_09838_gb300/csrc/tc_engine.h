@@ -21,6 +21,10 @@ struct EngineBase {
   virtual tc_status profile(int n, double* ms, std::string& err) = 0;
   virtual tc_status convergence(double* changes, int* stopped, long long* iters_run, std::string& err) = 0;
   virtual void release() = 0;
+  // one iteration captured as a graph (the caller owns and destroys it)
+  virtual tc_status capture_iteration(cudaGraph_t* out, std::string& err) = 0;
+  virtual cudaStream_t stream() const = 0;
+  virtual bool poisoned() const = 0;
 };
 
 EngineBase* make_engine_f32();

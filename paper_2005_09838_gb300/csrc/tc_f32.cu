@@ -1,6 +1,7 @@
 // FP32 engine: generic slab kernel here; the slab kernels specialised for a
 // tube length live in their own translation units (compiled in parallel).
 #include "tc_engine.cuh"
+#include "k_tc.cuh"
 
 namespace tc {
 
@@ -18,6 +19,32 @@ bool pick_slab<float>(int n2, int n3, int optin, SlabCfg<float>& cfg) {
 
 template <>
 void upload_twiddles<float>() {}
+
+template <>
+bool pick_tc<float>(int precision, bool split, TcKernels<float>& k) {
+  using namespace umma;
+  if (precision == TC_TF32) {
+    if (split) {
+      k = {k_qcon_tc<kTF32, true>, k_dcon_tc<kTF32, true>, k_zsyn_tc<kTF32, true>, qcon_tc_smem<kTF32, true>(),
+           dcon_tc_smem<kTF32, true>(), zsyn_tc_smem<kTF32, true>()};
+    } else {
+      k = {k_qcon_tc<kTF32, false>, k_dcon_tc<kTF32, false>, k_zsyn_tc<kTF32, false>, qcon_tc_smem<kTF32, false>(),
+           dcon_tc_smem<kTF32, false>(), zsyn_tc_smem<kTF32, false>()};
+    }
+    return true;
+  }
+  if (precision == TC_BF16) {
+    if (split) {
+      k = {k_qcon_tc<kBF16, true>, k_dcon_tc<kBF16, true>, k_zsyn_tc<kBF16, true>, qcon_tc_smem<kBF16, true>(),
+           dcon_tc_smem<kBF16, true>(), zsyn_tc_smem<kBF16, true>()};
+    } else {
+      k = {k_qcon_tc<kBF16, false>, k_dcon_tc<kBF16, false>, k_zsyn_tc<kBF16, false>, qcon_tc_smem<kBF16, false>(),
+           dcon_tc_smem<kBF16, false>(), zsyn_tc_smem<kBF16, false>()};
+    }
+    return true;
+  }
+  return false;
+}
 
 EngineBase* make_engine_f32() { return new Engine<float>(); }
 

@@ -18,6 +18,11 @@ bool pick_slab<double>(int n2, int n3, int optin, SlabCfg<double>& cfg) {
 template <>
 void upload_twiddles<double>() { fft::upload_tables<double>(); }
 
+template <>
+bool pick_tc<double>(int, bool, TcKernels<double>&) {
+  return false;
+}
+
 EngineBase* make_engine_f64() { return new Engine<double>(); }
 
 }  // namespace tc

@@ -176,17 +176,19 @@ struct GradEngine final : tc_grad {
       if (!err.empty()) return TC_ERR_NOMEM;
       d_.scratch = scratch;
     }
-    TCG_TRY(cudaFuncSetAttribute(slab_.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab_.smem));
+    TCG_TRY(allow_dynamic_smem((const void*)slab_.f, slab_.smem));
     qcon_ = pick_qcon_g<T>(rp_);
     dcon_ = pick_dcon<T>(rp_);
     qsmem_ = qcon_smem_bytes<T>(n2_, r_, rp_);
     dsmem_ = dcon_smem_bytes<T>(n1_, r_, rp_);
+    d_.yx_global = dsmem_ > (size_t)optin ? 1 : 0;
+    if (d_.yx_global) dsmem_ = dcon_smem_bytes<T>(n1_, r_, rp_, false);
     if (qsmem_ > (size_t)optin || dsmem_ > (size_t)optin) {
       err = "shared memory of the gradient kernels exceeds the device limit for these sizes";
       return TC_ERR_UNSUPPORTED;
     }
-    TCG_TRY(cudaFuncSetAttribute(qcon_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem_));
-    TCG_TRY(cudaFuncSetAttribute(dcon_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem_));
+    TCG_TRY(allow_dynamic_smem((const void*)qcon_, qsmem_));
+    TCG_TRY(allow_dynamic_smem((const void*)dcon_, dsmem_));
 
     std::vector<cx<T>> tw(n3_);
     for (int m = 0; m < n3_; ++m) {

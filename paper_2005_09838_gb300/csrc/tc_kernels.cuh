@@ -57,6 +57,9 @@ struct Dev {
   double* part_dw;   // [n1] partial sums of ||W~^{l+1} - W~^l||^2 over the half spectrum (weighted)
   cx<T>* dZt;        // [n1][S][n2] Z~^{l+1} - Z~^l (written by k_ystep while the test is on)
   double eps;
+  int yx_global;     // 1: k_ystep reads X~ of the slice from global memory (r n1 too large to stage)
+  cx<T>* Dpart;      // [S][ksplit][r][n2] partial D = X~'^H R~ of the tensor-core Y-step
+  int ksplit;
 };
 
 // True once the stopping test has fired: the iteration kernels return at once.

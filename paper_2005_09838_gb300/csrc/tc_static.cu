@@ -130,10 +130,11 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   SlabLayout lay = slab_layout<T>(n2, n3, false, true);
   const bool slabs_in_smem = lay.total <= (size_t)optin;
   if (!slabs_in_smem) lay = slab_layout<T>(n2, n3, false, false);
-  XLayout xl = xstep_layout<T>(n1, n2, r, true);
+  XLayout xl = xstep_layout_for<T>(n1, n2, r, rp, false, true);
   const bool xsmem = xl.total <= (size_t)optin;
-  if (!xsmem) xl = xstep_layout<T>(n1, n2, r, false);
-  const size_t ysm = ystep_smem_bytes<T>(n1, r, rp), qsm = qcon_smem_bytes<T>(n2, r, rp);
+  if (!xsmem) xl = xstep_layout_for<T>(n1, n2, r, rp, false, false);
+  const bool yxg = ystep_smem_bytes<T>(n1, r, rp) > (size_t)optin;
+  const size_t ysm = ystep_smem_bytes<T>(n1, r, rp, !yxg), qsm = qcon_smem_bytes<T>(n2, r, rp);
   if (xl.total > (size_t)optin || ysm > (size_t)optin || qsm > (size_t)optin)
     return sfail(TC_ERR_UNSUPPORTED, "shared memory of the slice kernels exceeds the device limit for these sizes");
 
@@ -178,18 +179,19 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   d.winv = winv;
   d.hinv = hinv;
   d.twg = twg;
-  d.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r * (double)std::numeric_limits<T>::epsilon();
+  d.yx_global = yxg ? 1 : 0;
+  d.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : default_rtol<T>(r, rp, false);
 
   // ---- kernels (generic mode-3 transform) ------------------------------------------------
   SlabFn<T> slab[3];
   slab_table<T, 0>(slab);
   YFn<T> ystep = pick_ystep<T>(rp);
   QFn<T> qcon = pick_qcon<T>(rp);
-  for (int m = 0; m < 3; ++m) cudaFuncSetAttribute(slab[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
-  XFn<T> xstep = pick_xstep<T>(rp);
-  cudaFuncSetAttribute(xstep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xl.total);
-  cudaFuncSetAttribute(ystep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysm);
-  cudaFuncSetAttribute(qcon, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
+  for (int m = 0; m < 3; ++m) allow_dynamic_smem((const void*)slab[m], lay.total);
+  XFn<T> xstep = pick_xstep_for<T>(rp, false);
+  allow_dynamic_smem((const void*)xstep, xl.total);
+  allow_dynamic_smem((const void*)ystep, ysm);
+  allow_dynamic_smem((const void*)qcon, qsm);
   const int sis = slabs_in_smem ? 1 : 0;
   const int fgrid = 4 * 152;
 
@@ -208,7 +210,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   slab[MODE_ITER]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 1);
   for (int it = 0; it < n_iters; ++it) {
     qcon<<<dim3(S, (n1 + 31) / 32), kSliceThreads, qsm, st>>>(d, Q);
-    xstep<<<S, kSliceThreads, xl.total, st>>>(d, Q, xsmem ? 1 : 0);
+    xstep<<<S, xstep_threads(rp), xl.total, st>>>(d, Q, xsmem ? 1 : 0);
     ystep<<<dim3(S, (n2 + 32 * ystep_cpl(rp) - 1) / (32 * ystep_cpl(rp))), kYThreads, ysm, st>>>(d);
     slab[MODE_ITER]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 0);
   }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libtctf2r.so")
 
 TC_OK, TC_ERR_ARG, TC_ERR_NOMEM, TC_ERR_CUDA, TC_ERR_NUMERIC, TC_ERR_TIMEOUT, TC_ERR_STATE, TC_ERR_UNSUPPORTED = range(8)
 TC_FP64, TC_FP32, TC_TF32, TC_BF16 = range(4)
+TC_FLAG_SINGLE_PASS = 1
 TC_STEP_EXACT, TC_STEP_SCALED = range(2)
 
 STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_ARG", 2: "TC_ERR_NOMEM", 3: "TC_ERR_CUDA", 4: "TC_ERR_NUMERIC",
@@ -84,6 +85,14 @@ def load(path: str | None = None):
     lib.tc_grad_eval.restype = ctypes.c_int
     lib.tc_grad_free.argtypes = [P]
     lib.tc_grad_free.restype = ctypes.c_int
+    lib.tc_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int32, P]
+    lib.tc_batch_create.restype = ctypes.c_int
+    lib.tc_batch_iterate.argtypes = [P, ctypes.c_int32]
+    lib.tc_batch_iterate.restype = ctypes.c_int
+    lib.tc_batch_branches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.tc_batch_branches.restype = ctypes.c_int
+    lib.tc_batch_free.argtypes = [P]
+    lib.tc_batch_free.restype = ctypes.c_int
     lib.tc_free.argtypes = [P]
     lib.tc_free.restype = ctypes.c_int
     lib.tc_last_error.argtypes = []
@@ -115,8 +124,8 @@ def _ptr(a) -> int | None:
 
 
 def make_params(n1, n2, n3, r, mu=0.0, rho1=0.0, rho2=0.0, precision=TC_FP32, step=TC_STEP_EXACT,
-                alpha=1.0, beta=1.0, eps=0.0, pinv_rtol=0.0) -> tc_params:
-    return tc_params(n1, n2, n3, r, precision, mu, rho1, rho2, step, 0, alpha, beta, eps, pinv_rtol)
+                alpha=1.0, beta=1.0, eps=0.0, pinv_rtol=0.0, flags=0) -> tc_params:
+    return tc_params(n1, n2, n3, r, precision, mu, rho1, rho2, step, flags, alpha, beta, eps, pinv_rtol)
 
 
 class Completion:
@@ -183,6 +192,44 @@ class Completion:
         if self._ctx:
             self._lib.tc_free(self._ctx)
             self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Batched form (tc_batch_*): the given Completion contexts advanced by one
+    CUDA graph launch per iteration.  The contexts stay usable (results,
+    objective) and must outlive the batch."""
+
+    def __init__(self, completions, stream: int | None = None):
+        self._lib = load()
+        self._members = list(completions)
+        arr = (ctypes.c_void_p * len(self._members))(*[c._ctx.value for c in self._members])
+        self._b = ctypes.c_void_p()
+        _check(self._lib.tc_batch_create(ctypes.byref(self._b), arr, len(self._members), stream))
+
+    def iterate(self, n: int):
+        _check(self._lib.tc_batch_iterate(self._b, int(n)))
+
+    def branches(self) -> int:
+        k = ctypes.c_int32(0)
+        _check(self._lib.tc_batch_branches(self._b, ctypes.byref(k)))
+        return k.value
+
+    def close(self):
+        if self._b:
+            self._lib.tc_batch_free(self._b)
+            self._b = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -63,8 +63,9 @@ def test_params_layout_matches_header(tmp_path):
     (dict(r=9), "TC_ERR_ARG"),       # r > n2 = 8
     (dict(mu=-1.0), "TC_ERR_ARG"),
     (dict(rho2=float("nan")), "TC_ERR_ARG"),
-    (dict(precision=2), "TC_ERR_UNSUPPORTED"),
     (dict(precision=9), "TC_ERR_ARG"),
+    (dict(flags=1), "TC_ERR_ARG"),               # single pass is for TC_TF32 / TC_BF16 only
+    (dict(precision=2, flags=2), "TC_ERR_ARG"),  # unknown flag bit
     (dict(step=1, alpha=0.0), "TC_ERR_ARG"),     # scaled steps need alpha, beta > 0
     (dict(step=1, beta=float("inf")), "TC_ERR_ARG"),
     (dict(step=2), "TC_ERR_ARG"),

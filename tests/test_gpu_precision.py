@@ -1,0 +1,80 @@
+"""Precision form (TC_TF32 / TC_BF16 over FP32 data) against the FP64 oracle.
+
+For r > 16 the contraction Q = R~Y~^H runs on the tensor cores (tcgen05)
+with TF32 or BF16 operands and FP32 accumulation; the r x r pseudo-inverses
+of every slice are taken in FP64 storage.  Bar for the default (operands
+split into a rounded part and a rounded remainder): relative Frobenius error
+of W <= 1e-3 against the oracle, relative error of f0 <= 1e-3, recovery NMSE
+within 1e-4 of the oracle's.  Single-pass operands carry the format's
+rounding (2^-11 TF32, 2^-8 BF16) into every contraction; their error is
+printed and held to a loose bound only.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import method as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-3
+SETTING = (1e-3, 1e-3, 1e-1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_09838_gb300 import build
+    build.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _pair(w, precision, iters, single_pass=False):
+    from paper_2005_09838_gb300 import api
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    ref = O.tctf2r(inst["G"], inst["mask"], w.r, *SETTING, inst["Y0"], iters=iters)
+    got = api.complete(inst["G"], inst["mask"], inst["Y0"], w.r, iters, *SETTING, precision,
+                       single_pass=single_pass)
+    return inst, ref, got
+
+
+def _check(inst, ref, got, tol, label):
+    e_w = _rel(got["W"], ref["W"])
+    e_f = abs(got["f0"] - ref["f0"]) / abs(ref["f0"])
+    d_nmse = abs(wl.nmse(inst["M"], got["W"], inst["mask"]) - wl.nmse(inst["M"], ref["W"], inst["mask"]))
+    print(f"{label}: |W - W_ref| / |W_ref| = {e_w:.2e}, f0 {e_f:.2e}, NMSE difference {d_nmse:.2e}")
+    assert e_w <= tol, label
+    assert e_f <= tol, label
+    return d_nmse
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("shape,r,obs", [
+    ((200, 96, 12), 32, 0.3),   # two row tiles (ragged), three K chunks
+    ((529, 40, 8), 24, 0.3),    # r padded to 32 on the tensor core, n1 = 529 (five tiles)
+    ((64, 48, 7), 8, 0.5),      # r <= 16: FP32 contractions, FP64 solves in registers
+])
+def test_precision_form_matches_oracle(precision, shape, r, obs):
+    w = wl.custom(*shape, r, obs, seed=7000 + shape[0] + r, iters=10)
+    inst, ref, got = _pair(w, precision, w.iters)
+    assert _check(inst, ref, got, TOL, f"{precision} {shape} r={r}") <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_c3_full_size_three_iterations(precision):
+    # the precision-form workload (529 x 96 x 112, r = 32, 30% observed)
+    w = wl.c3(0.3)
+    inst, ref, got = _pair(w, precision, 3)
+    assert _check(inst, ref, got, TOL, f"C3 {precision}") <= 1e-4
+
+
+@pytest.mark.parametrize("precision,bound", [("tf32", 2e-2), ("bf16", 1e-1)])
+def test_single_pass_error_is_reported(precision, bound):
+    w = wl.custom(200, 96, 12, 32, 0.3, seed=7400, iters=10)
+    inst, ref, got = _pair(w, precision, w.iters, single_pass=True)
+    _check(inst, ref, got, bound, f"single-pass {precision}")
