@@ -10,6 +10,18 @@ L2 is flushed (512 MiB write) before every timed step.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the same workload instead (bounded samples on the host cores).
+
+Two more forms, each one JSON line of its own (not the default):
+``--form precision``: the 529 x 96 x 112 tensor (529 OD pairs x 96
+fifteen-minute slots x 112 days), tubal rank 32, 30% observed; the precision
+form (TF32 / BF16 tensor-core contractions, FP64-storage solves) against the
+plain FP32 path on the same resident instance, 30 iterations per step, with
+the recovery NMSE of each against the FP64 path.
+``--form batched``: 64 seeded instances with n1 in [64, 1024], n2 in
+[96, 288], n3 in [28, 168], r in [4, 32], 10-60% observed, advanced together
+by one graph launch per iteration (tc_batch_*), TF32 tensor-core
+contractions where r > 16; compared with the same contexts iterated one after
+the other and with the plain FP32 batch.
 """
 from __future__ import annotations
 
@@ -45,6 +57,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nmse", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched"])
     return ap.parse_args()
 
 
@@ -159,10 +172,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SLAB_SOURCES = ("k_slab_f.cuh", "k_slab.cuh", "fft_reg.cuh", "tc_common.cuh", "tc_kernels.cuh", "tc_f32_168.cu")
+
+
 def src_hash():
+    """Hash of the sources the 168-point slab kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_09838_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SLAB_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -347,10 +364,172 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# precision form
+# ---------------------------------------------------------------------------
+def _resident(tc, torch, dev, w, inst, prec, flags, sptr):
+    g = torch.from_numpy(wl.to_colmajor(inst["G"], np.float32 if prec != tc.TC_FP64 else np.float64)).to(dev)
+    m = torch.from_numpy(wl.to_colmajor(inst["mask"], np.uint8)).to(dev)
+    y = torch.from_numpy(wl.to_colmajor(inst["Y0"], np.float32 if prec != tc.TC_FP64 else np.float64)).to(dev)
+    p = tc.make_params(w.n1, w.n2, w.n3, w.r, WEIGHTS["mu"], WEIGHTS["rho1"], WEIGHTS["rho2"], prec, flags=flags)
+    torch.cuda.synchronize()
+    return tc.Completion(p, g, m, y, on_device=True, stream=sptr)
+
+
+def _timed(torch, stream, flush, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return sum(ms)
+
+
+def run_precision(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2005_09838_gb300 import build as _b
+    _b.build()
+    from paper_2005_09838_gb300 import tc, api
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    w = wl.c3(0.3)
+    iters = w.iters
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    forms = {"fp32": (tc.TC_FP32, 0), "tf32": (tc.TC_TF32, 0), "bf16": (tc.TC_BF16, 0),
+             "tf32_single_pass": (tc.TC_TF32, tc.TC_FLAG_SINGLE_PASS),
+             "bf16_single_pass": (tc.TC_BF16, tc.TC_FLAG_SINGLE_PASS)}
+    rates, kern = {}, {}
+    with ClockSampler(0) as clk:
+        for name, (prec, fl) in forms.items():
+            # one completion (the configured 30 iterations from the initial point) per step,
+            # each on a context initialised before the timed region
+            cs = [_resident(tc, torch, dev, w, inst, prec, fl, sptr) for _ in range(args.warmup + args.steps)]
+            it = iter(cs)
+            ms = _timed(torch, stream, flush, lambda: next(it).iterate(iters, count=False), args.steps, args.warmup)
+            rates[name] = iters * args.steps / (ms / 1e3)
+            kern[name] = dict(zip(("qcon", "xstep", "ystep", "slab"), cs[0].profile(10)))
+            for c in cs:
+                c.close()
+    nmse = {}
+    if not args.no_nmse:
+        for name, prec in (("fp64", "fp64"), ("fp32", "fp32"), ("tf32", "tf32"), ("bf16", "bf16")):
+            o = api.complete(inst["G"], inst["mask"], inst["Y0"], w.r, iters, *WEIGHTS.values(), prec, objective=False)
+            nmse[name] = wl.nmse(inst["M"], o["W"], inst["mask"])
+    N = w.N
+    line = {"metric": "completion iters/s, precision form (TF32 tensor-core contractions, FP64-storage solves) "
+                      "vs plain FP32, 529x96x112 r=32",
+            "value": rates["tf32"], "unit": "iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": iters * 1e3 / rates["tf32"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "tf32 (split operands) / f32", "data": "synthetic",
+            "config": {"workload": "529x96x112 traffic tensor (OD x 15-min slots x days), tubal rank 32, 30% observed",
+                       "iters_per_step": iters, "weights": WEIGHTS, "l2": "flushed before every timed step",
+                       "entries_per_s": rates["tf32"] * N},
+            "forms_iters_per_s": rates, "speedup_vs_fp32": {k: v / rates["fp32"] for k, v in rates.items()},
+            "kernel_ms_after_30_iters": kern, "nmse": nmse,
+            "nmse_abs_diff_vs_fp64": {k: abs(v - nmse["fp64"]) for k, v in nmse.items()} if nmse else None,
+            "gpu_launches_per_iter": 6, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+BATCH = 64
+
+
+def batch_workloads():
+    rng = np.random.default_rng(2005_09838 + 5000)
+    out = []
+    for q in range(BATCH):
+        n1, n2, n3 = int(rng.integers(64, 1025)), int(rng.integers(96, 289)), int(rng.integers(28, 169))
+        r = int(rng.integers(4, 33))
+        obs = float(rng.uniform(0.1, 0.6))
+        out.append(wl.custom(n1, n2, n3, r, obs, seed=2005_09838 + 5000 + q, period=n2,
+                             name=f"batch {q}: {n1}x{n2}x{n3} r={r}"))
+    return out
+
+
+def _gen32(w):
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    return (wl.to_colmajor(inst["G"], np.float32), wl.to_colmajor(inst["mask"], np.uint8),
+            wl.to_colmajor(inst["Y0"], np.float32))
+
+
+def run_batched(args):
+    import multiprocessing as mp
+    ws = batch_workloads()
+    # inputs drawn on the host cores before any CUDA call (spawned workers)
+    with mp.get_context("spawn").Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
+        data = pool.map(_gen32, ws)
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2005_09838_gb300 import build as _b
+    _b.build()
+    from paper_2005_09838_gb300 import tc
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    iters = 10
+    entries = sum(w.N for w in ws)
+
+    def contexts(mixed):
+        cs = []
+        for w, (g, m, y) in zip(ws, data):
+            prec = tc.TC_TF32 if (mixed and w.r > 16) else tc.TC_FP32
+            p = tc.make_params(w.n1, w.n2, w.n3, w.r, WEIGHTS["mu"], WEIGHTS["rho1"], WEIGHTS["rho2"], prec)
+            cs.append(tc.Completion(p, torch.from_numpy(g).to(dev), torch.from_numpy(m).to(dev),
+                                    torch.from_numpy(y).to(dev), on_device=True, stream=sptr))
+            torch.cuda.synchronize()
+        return cs
+
+    res = {}
+    with ClockSampler(0) as clk:
+        for label, mixed in (("mixed", True), ("fp32", False)):
+            cs = contexts(mixed)
+            with tc.Batch(cs, stream=sptr) as B:
+                B.iterate(2 * 4)  # tuning trials (two per candidate branch count), real iterations
+                ms = _timed(torch, stream, flush, lambda: B.iterate(iters), args.steps, args.warmup)
+                res[f"batch_{label}"] = BATCH * iters * args.steps / (ms / 1e3)
+                res[f"branches_{label}"] = B.branches()
+            ms = _timed(torch, stream, flush, lambda: [c.iterate(iters, count=False) for c in cs], args.steps,
+                        args.warmup)
+            res[f"sequential_{label}"] = BATCH * iters * args.steps / (ms / 1e3)
+            for c in cs:
+                c.close()
+            torch.cuda.synchronize()
+    value = res["batch_mixed"]
+    line = {"metric": "instance-iterations/s, batched form (64 heterogeneous completions, one graph launch per "
+                      "iteration, TF32 tensor cores where r > 16)",
+            "value": value, "unit": "instance-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": BATCH * iters * 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "tf32 (split operands, r > 16) / f32", "data": "synthetic",
+            "config": {"workload": "64 traffic tensors, n1 64-1024, n2 96-288, n3 28-168, r 4-32, 10-60% observed",
+                       "instances": [w.name for w in ws], "iters_per_step": iters, "entries_total": entries,
+                       "entries_per_s": value * entries / BATCH, "l2": "flushed before every timed step"},
+            "rates": res, "speedup_vs_sequential_fp32": value / res["sequential_fp32"],
+            "speedup_vs_batched_fp32": value / res["batch_fp32"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.form == "precision":
+        run_precision(args)
+    elif args.form == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

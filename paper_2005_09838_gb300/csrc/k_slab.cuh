@@ -220,10 +220,13 @@ __device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int n3, c
   const T inv = T(1) / T(n3);
   for (int l = 0; l < n3; ++l) {
     T acc = spec[0].re;
+    int idx = l;  // k l mod n3, advanced by l per k
     for (int k = 1; k <= kmax; ++k) {
-      const cx<T> w = twg[(int)(((long long)k * l) % n3)];
+      const cx<T> w = twg[idx];
       const cx<T> v = spec[k * sstride];
       acc += T(2) * (v.re * w.re + v.im * w.im);  // 2 Re(v conj(w))
+      idx += l;
+      if (idx >= n3) idx -= n3;
     }
     if (even) acc += ((l & 1) ? -spec[(S - 1) * sstride].re : spec[(S - 1) * sstride].re);
     spat[l] = acc * inv;
@@ -239,11 +242,14 @@ __device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, 
   const int S = n3 / 2 + 1;
   for (int k = 0; k < S; ++k) {
     cx<T> acc = {T(0), T(0)};
+    int idx = 0;  // k l mod n3, advanced by k per l
     for (int l = 0; l < n3; ++l) {
-      const cx<T> w = twg[(int)(((long long)k * l) % n3)];
+      const cx<T> w = twg[idx];
       const T x = spat[l];
       acc.re += x * w.re;
       acc.im += x * w.im;
+      idx += k;
+      if (idx >= n3) idx -= n3;
     }
     if (k == 0 || (2 * k == n3)) acc.im = T(0);
     const cx<T> rn = zsub ? acc - zsub[k * stride] : acc;

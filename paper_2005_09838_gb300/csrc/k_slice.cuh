@@ -25,9 +25,9 @@ namespace tc {
 // piv: 3*r complex values; sred: 4 values.  Every thread of the block must
 // call it.  Returns (block-uniform) 1 if the inverse path was taken.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
-                                        T rtol, T* lmax_out);
+template <typename TS, bool DF>
+__device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
+                                       int r, TS rtol, TS* lmax_out);
 
 // Frobenius norm of the r x r block at column col0 of a row-major matrix with
 // leading dimension ld, by one warp.
@@ -41,6 +41,20 @@ __device__ inline T warp_frob(const cx<T>* M, int ld, int col0, int r) {
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return sqrt(s);
+}
+
+// The same in FP32 arithmetic (a certificate needs only a few digits; the
+// FP64 pipe of this part is slow).
+template <typename T>
+__device__ inline float warp_frob_lowp(const cx<T>* M, int r) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  for (int e = lane; e < r * r; e += 32) {
+    const float a = (float)M[e].re, b = (float)M[e].im;
+    s = fmaf(a, a, fmaf(b, b, s));
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return sqrtf(s);
 }
 
 // 1/a.  FP64: a correctly rounded FP32 seed and two Newton steps
@@ -62,36 +76,42 @@ __device__ __forceinline__ T tiny_pivot() {
   return sizeof(T) == 8 ? T(1e-300) : T(1e-37f);
 }
 
-// In-place Gauss-Jordan inverse of the r x r matrix W (row-major) without
-// pivoting: at pivot p, a_pp <- 1/a_pp, a_pj <- a_pj / a_pp, a_ij <- a_ij -
-// a_ip a_pj and a_ip <- -a_ip / a_pp (r^3 complex multiply-adds, half of the
-// augmented form).  Threads [t0, t0 + nt) of the caller; sync() orders the
-// steps among them.  Returns 0 when a pivot is not positive.
+// Gauss-Jordan inverse of the r x r matrix W (row-major) without pivoting:
+// at pivot p, a_pp <- 1/a_pp, a_pj <- a_pj / a_pp, a_ij <- a_ij - a_ip a_pj /
+// a_pp and a_ip <- -a_ip / a_pp (r^3 complex multiply-adds).  W holds 2 r^2
+// values: its halves alternate as source and destination, so one barrier per
+// pivot suffices; piv[0], piv[1] carry the next pivot's reciprocal (re) and a
+// validity flag (im), set by the thread that forms that pivot.  The inverse
+// ends in the first half.  Threads [t, t + nt) of the caller; sync() orders
+// the steps among them.  Returns 0 when a pivot is not positive.
 template <typename T, typename Sync>
 __device__ __forceinline__ int gauss_jordan_inplace(cx<T>* W, cx<T>* piv, int r, int t, int nt, Sync sync) {
-  cx<T>* colp = piv;
-  cx<T>* rowp = piv + r;
+  const int rr = r * r;
+  auto pivot_info = [](T pv) {
+    const bool ok = (pv > tiny_pivot<T>()) && isfinite(pv);
+    return cx<T>{ok ? rcp_refined(pv) : T(0), ok ? T(1) : T(0)};
+  };
+  if (t == 0) piv[0] = pivot_info(W[0].re);
+  sync();
   for (int p = 0; p < r; ++p) {
-    const T pv = W[p * r + p].re;
-    if (!((pv > tiny_pivot<T>()) && isfinite(pv))) return 0;
-    const T ip = rcp_refined(pv);
-    for (int e = t; e < 2 * r; e += nt) {
-      if (e < r) {
-        colp[e] = W[e * r + p];
-      } else {
-        const int j = e - r;
-        rowp[j] = (j == p) ? cx<T>{ip, T(0)} : W[p * r + j] * ip;
-      }
-    }
-    sync();
-    for (int e = t; e < r * r; e += nt) {
+    const cx<T>* src = W + (p & 1) * rr;
+    cx<T>* dst = W + ((p + 1) & 1) * rr;
+    const cx<T> pinfo = piv[p & 1];
+    if (pinfo.im == T(0)) return 0;
+    const T ip = pinfo.re;
+    for (int e = t; e < rr; e += nt) {
       const int i = e / r, j = e - i * r;
       cx<T> v;
-      if (i == p) v = rowp[j];
-      else if (j == p) v = colp[i] * (-ip);
-      else v = W[e] - cmul(colp[i], rowp[j]);
-      W[e] = v;
+      if (i == p) v = (j == p) ? cx<T>{ip, T(0)} : src[p * r + j] * ip;
+      else if (j == p) v = src[i * r + p] * (-ip);
+      else v = src[e] - cmul(src[i * r + p], src[p * r + j] * ip);
+      dst[e] = v;
+      if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = pivot_info(v.re);
     }
+    sync();
+  }
+  if (r & 1) {
+    for (int e = t; e < rr; e += nt) W[e] = W[rr + e];
     sync();
   }
   return 1;
@@ -124,7 +144,7 @@ __device__ __forceinline__ df df_add(df a, df b) {
 }
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = a.hi * b.hi;
+  const float p = __fmul_rn(a.hi, b.hi);  // not contracted: fmaf below recovers its rounding error
   const float e = fmaf(a.hi, b.hi, -p) + (a.hi * b.lo + a.lo * b.hi);
   return df_norm(p, e);
 }
@@ -142,49 +162,48 @@ __device__ __forceinline__ df df_rcp(df a) {
 }
 
 // gauss_jordan_inplace on an FP64 matrix, with the arithmetic in df64 (the
-// matrix is converted in place, eliminated and converted back; no FP64
-// instruction in the elimination itself).
+// matrix is converted, eliminated and converted back; no FP64 instruction in
+// the elimination itself).
 template <typename Sync>
 __device__ __forceinline__ int gauss_jordan_inplace_df(cx<double>* W64, cx<double>* piv, int r, int t, int nt,
                                                        Sync sync) {
+  const int rr = r * r;
   dfc* W = reinterpret_cast<dfc*>(W64);
-  dfc* colp = reinterpret_cast<dfc*>(piv);
-  dfc* rowp = colp + r;
-  for (int e = t; e < r * r; e += nt) {
+  dfc* pv2 = reinterpret_cast<dfc*>(piv);
+  auto pivot_info = [](df pv) {
+    const bool ok = (pv.hi > 1e-30f) && isfinite(pv.hi);
+    return dfc{ok ? df_rcp(pv) : df{0.f, 0.f}, df{ok ? 1.f : 0.f, 0.f}};
+  };
+  if (t == 0) pv2[0] = pivot_info(df_from(W64[0].re));
+  for (int e = t; e < rr; e += nt) {
     const cx<double> v = W64[e];
     W[e] = dfc{df_from(v.re), df_from(v.im)};
   }
   sync();
   int ok = 1;
   for (int p = 0; p < r; ++p) {
-    const df pv = W[p * r + p].re;
-    if (!((pv.hi > 1e-30f) && isfinite(pv.hi))) {
+    const dfc* src = W + (p & 1) * rr;
+    dfc* dst = W + ((p + 1) & 1) * rr;
+    const dfc pinfo = pv2[p & 1];
+    if (pinfo.im.hi == 0.f) {
       ok = 0;
       break;
     }
-    const df ip = df_rcp(pv);
-    for (int e = t; e < 2 * r; e += nt) {
-      if (e < r) {
-        colp[e] = W[e * r + p];
-      } else {
-        const int j = e - r;
-        rowp[j] = (j == p) ? dfc{ip, df{0.f, 0.f}} : dfc_scale(W[p * r + j], ip);
-      }
-    }
-    sync();
-    const df nip = df_neg(ip);
-    for (int e = t; e < r * r; e += nt) {
+    const df ip = pinfo.re, nip = df_neg(ip);
+    for (int e = t; e < rr; e += nt) {
       const int i = e / r, j = e - i * r;
       dfc v;
-      if (i == p) v = rowp[j];
-      else if (j == p) v = dfc_scale(colp[i], nip);
-      else v = dfc_sub(W[e], dfc_mul(colp[i], rowp[j]));
-      W[e] = v;
+      if (i == p) v = (j == p) ? dfc{ip, df{0.f, 0.f}} : dfc_scale(src[p * r + j], ip);
+      else if (j == p) v = dfc_scale(src[i * r + p], nip);
+      else v = dfc_sub(src[e], dfc_mul(src[i * r + p], dfc_scale(src[p * r + j], ip)));
+      dst[e] = v;
+      if (i == p + 1 && j == p + 1) pv2[(p + 1) & 1] = pivot_info(v.re);
     }
     sync();
   }
-  for (int e = t; e < r * r; e += nt) {
-    const dfc v = W[e];
+  const dfc* res = W + (r & 1) * rr;
+  for (int e = t; e < rr; e += nt) {
+    const dfc v = res[e];
     W64[e] = cx<double>{df_to(v.re), df_to(v.im)};
   }
   sync();
@@ -254,7 +273,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
   int ok;
   if (force_eig) {
     // the eigendecomposition is wanted for lambda_max (scaled steps): sred[2]
-    if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
+    jacobi_fallback<T, DF>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
     __syncthreads();
     return 0;
   }
@@ -282,7 +301,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
   } else {
     for (int e = tid; e < r * r; e += nt) W[e] = A[e];
     if (tid < 32) {
-      const T an = warp_frob(A, r, 0, r);
+      const T an = DF ? (T)warp_frob_lowp(A, r) : warp_frob(A, r, 0, r);
       if (tid == 0) sred[0] = an;
     }
     __syncthreads();
@@ -293,7 +312,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
       else ok = gauss_jordan_inplace<T>(W, piv, r, tid, nt, []() { __syncthreads(); });
     }
     if (tid < 32) {
-      const T in = ok ? warp_frob(W, r, 0, r) : T(0);
+      const T in = ok ? (DF ? (T)warp_frob_lowp(W, r) : warp_frob(W, r, 0, r)) : T(0);
       if (tid == 0) sred[1] = (ok && isfinite(in) && anorm * in < T(0.5) / rtol) ? T(1) : T(0);
     }
     __syncthreads();
@@ -311,45 +330,45 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
     }
   }
   __syncthreads();
-  if (tid < 32) warp_jacobi_pinv<T>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
+  jacobi_fallback<T, DF>(A, Ap, P, V, W, piv, r, rtol, sred + 2);
   __syncthreads();
   return 0;
 }
 
 // Parallel cyclic complex Jacobi eigendecomposition A = V diag(lambda) V^* by
-// one warp, then A^+ and P = A A^+ with the cutoff rule.  Each round rotates
-// the disjoint pairs of a round-robin schedule (m - 1 rounds of m/2 pairs,
-// m = r rounded up to even, index r a dummy when r is odd); a rotation is
-// skipped when |a_pq| <= 4 u max(|a_pp|, |a_qq|) (u the unit roundoff), and
-// the sweeps stop after one without rotations.
+// the whole block, then A^+ and P = A A^+ with the cutoff rule.  Each round
+// rotates the disjoint pairs of a round-robin schedule (m - 1 rounds of m/2
+// pairs, m = r rounded up to even, index r a dummy when r is odd): the pair
+// threads form the rotations, then all threads apply them to the columns
+// (W J, V J) and to the rows (J^H W J).  A rotation is skipped when
+// |a_pq| <= 4 u max(|a_pp|, |a_qq|) (u the unit roundoff), and the sweeps stop
+// after one without rotations.
 template <typename T>
-__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
-                                        T rtol, T* lmax_out) {
-  const int lane = threadIdx.x & 31;
+__device__ inline void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+                                         T rtol, T* lmax_out) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
   const int m = (r + 1) & ~1, np = m / 2;
   // rotation of pair k: piv[2k] = (cs, sn), piv[2k + 1] = unit phase u; rows p, q in rpq
-  int* rpq = reinterpret_cast<int*>(piv + 2 * np);  // 2 ints per pair (fits in the third r values)
-  __syncwarp();
-  for (int e = lane; e < r * r; e += 32) {
+  int* rpq = reinterpret_cast<int*>(piv + 2 * np);
+  for (int e = tid; e < r * r; e += nt) {
     W[e] = A[e];
     const int i = e / r, j = e - i * r;
     V[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
   }
-  __syncwarp();
+  __syncthreads();
   for (int sweep = 0; sweep < 30; ++sweep) {
     bool any = false;
     for (int round = 0; round < m - 1; ++round) {
-      // ---- rotations of this round (lane k < np) ----
-      bool rot = false;
-      if (lane < np) {
+      int rot = 0;
+      if (tid < np) {
         int a, b;
-        if (lane == 0) {
+        if (tid == 0) {
           a = round;
           b = m - 1;
         } else {
-          a = (round + lane) % (m - 1);
-          b = (round - lane + m - 1) % (m - 1);
+          a = (round + tid) % (m - 1);
+          b = (round - tid + m - 1) % (m - 1);
         }
         const int p = min(a, b), q = max(a, b);
         T cs = T(1), sn = T(0);
@@ -368,20 +387,18 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
             cs = rsqrt(T(1) + t * t);
             sn = t * cs;
-            rot = true;
+            rot = 1;
           }
         }
-        piv[2 * lane] = cx<T>{cs, sn};
-        piv[2 * lane + 1] = uu;
-        rpq[2 * lane] = p;
-        rpq[2 * lane + 1] = (q < r) ? q : -1;
+        piv[2 * tid] = cx<T>{cs, sn};
+        piv[2 * tid + 1] = uu;
+        rpq[2 * tid] = p;
+        rpq[2 * tid + 1] = (q < r) ? q : -1;
       }
-      rot = __any_sync(0xffffffffu, rot);
-      __syncwarp();
-      if (!rot) continue;
+      if (!__syncthreads_or(rot)) continue;
       any = true;
       // ---- columns: W J and V J (item = row i, pair k) ----
-      for (int e = lane; e < r * np; e += 32) {
+      for (int e = tid; e < r * np; e += nt) {
         const int k = e / r, i = e - k * r;
         const int p = rpq[2 * k], q = rpq[2 * k + 1];
         if (q < 0) continue;
@@ -395,9 +412,9 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
         V[i * r + p] = vip * cs - cmulc(viq, uu) * sn;
         V[i * r + q] = cmul(vip, uu) * sn + viq * cs;
       }
-      __syncwarp();
+      __syncthreads();
       // ---- rows: J^H (W J) (item = pair k, column j) ----
-      for (int e = lane; e < r * np; e += 32) {
+      for (int e = tid; e < r * np; e += nt) {
         const int k = e / r, j = e - k * r;
         const int p = rpq[2 * k], q = rpq[2 * k + 1];
         if (q < 0) continue;
@@ -407,7 +424,7 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
         W[p * r + j] = apj * cs - cmul(aqj, uu) * sn;
         W[q * r + j] = cmulc(apj, uu) * sn + aqj * cs;
       }
-      __syncwarp();
+      __syncthreads();
     }
     if (!any) break;
   }
@@ -415,9 +432,8 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
   T lmax = T(0);
   for (int i = 0; i < r; ++i) lmax = fmax(lmax, W[i * r + i].re);
   const T cut = rtol * lmax;
-  if (lane == 0) *lmax_out = lmax;
-  __syncwarp();
-  for (int e = lane; e < r * r; e += 32) {
+  if (tid == 0) *lmax_out = lmax;
+  for (int e = tid; e < r * r; e += nt) {
     const int i = e / r, j = e - i * r;
     cx<T> sa = {T(0), T(0)}, sp = {T(0), T(0)};
     for (int mm = 0; mm < r; ++mm) {
@@ -431,7 +447,39 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
     Ap[e] = sa;
     P[e] = sp;
   }
-  __syncwarp();
+  __syncthreads();
+}
+
+// The eigendecomposition fallback of block_pinv_herm.  For the FP64-storage
+// solves of an FP32 engine (DF) it runs in FP32 on the FP32 pipes (the FP64
+// pipe of this part is 1/64 of it), with the cutoff raised to at least
+// r 2^-23 lambda_max: the Gram was accumulated in FP32 and cannot resolve
+// smaller eigenvalues.
+template <typename TS, bool DF>
+__device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
+                                       int r, TS rtol, TS* lmax_out) {
+  if constexpr (DF && sizeof(TS) == 8) {
+    const int tid = threadIdx.x, nt = blockDim.x, rr = r * r;
+    cx<float>* Af = reinterpret_cast<cx<float>*>(W);  // W holds 4 r^2 float pairs
+    cx<float>* Wf = Af + rr;
+    cx<float>* Vf = Wf + rr;
+    cx<float>* Pf = Vf + rr;
+    cx<float>* Apf = reinterpret_cast<cx<float>*>(V);  // V holds 2 r^2 float pairs
+    float* lmf = reinterpret_cast<float*>(Apf + rr);
+    cx<float>* pivf = reinterpret_cast<cx<float>*>(piv);
+    for (int e = tid; e < rr; e += nt) Af[e] = cx<float>{(float)A[e].re, (float)A[e].im};
+    __syncthreads();
+    const float rt = fmaxf((float)rtol, (float)r * 1.1920929e-7f);
+    block_jacobi_pinv<float>(Af, Apf, Pf, Vf, Wf, pivf, r, rt, lmf);
+    for (int e = tid; e < rr; e += nt) {
+      Ap[e] = cx<TS>{(TS)Apf[e].re, (TS)Apf[e].im};
+      P[e] = cx<TS>{(TS)Pf[e].re, (TS)Pf[e].im};
+    }
+    if (tid == 0) *lmax_out = (TS)*lmf;
+    __syncthreads();
+  } else {
+    block_jacobi_pinv<TS>(A, Ap, P, V, W, piv, r, rtol, lmax_out);
+  }
 }
 
 // Upper-triangle task index -> (s, u), s <= u.
@@ -620,9 +668,8 @@ __host__ __device__ inline XLayout xstep_layout(int n1, int n2, int r, bool arra
     L.ts = off;
     off = align_up(off + sizeof(cx<T>) * r * n1, 16);
   }
-  // Gram staging rows: in the Q array when it is in shared memory and large
-  // enough (Q is dead once B is formed), else a region of their own
-  if (arrays_in_smem && n1 >= 2 * kGramLd) {
+  // Gram staging rows, used only when the arrays are not resident
+  if (arrays_in_smem) {
     L.gs = L.qs;
   } else {
     L.gs = off;
@@ -724,7 +771,7 @@ __device__ __forceinline__ cx<T> cvt(cx<S> v) {
 __host__ __device__ constexpr int xstep_threads(int rp) { return rp > 16 ? 1024 : kSliceThreads; }
 
 template <typename T, int RP, typename TS = T>
-__global__ void __launch_bounds__(xstep_threads(RP)) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
+__global__ void __launch_bounds__(xstep_threads(RP), 1) k_xstep(Dev<T> d, const cx<T>* __restrict__ Qin, int arrays_in_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (converged(d)) return;
   const int k = blockIdx.x;
@@ -802,7 +849,7 @@ __global__ void __launch_bounds__(xstep_threads(RP)) k_xstep(Dev<T> d, const cx<
   }
   __syncthreads();
   {
-    constexpr int SB = RP < 8 ? RP : 8;
+    constexpr int SB = RP < 8 ? RP : (RP == 8 ? 2 : 8);  // enough items to fill the CTA at small n1
     const int nsb = (r + SB - 1) / SB;
     for (int e = tid; e < nsb * n1; e += blockDim.x) {
       const int sb = e / n1, i = e - sb * n1, s0 = sb * SB;
@@ -866,7 +913,26 @@ __global__ void __launch_bounds__(xstep_threads(RP)) k_xstep(Dev<T> d, const cx<
     for (int t = 0; t < MT; ++t) a0[t] = hh[t] = dd[t] = cx<T>{T(0), T(0)};
     cx<T>* gx = reinterpret_cast<cx<T>*>(smem + lay.gs);  // [r][kGramLd] rows i0 .. i0 + kGramRows of X~'
     cx<T>* go = gx + (size_t)r * kGramLd;                 // [r][kGramLd] rows i0 .. of X~
-    for (int i0 = 0; i0 < n1; i0 += kGramRows) {
+    if (arrays_in_smem) {
+      // X~' and X~ are resident: read them in place
+#pragma unroll
+      for (int t = 0; t < MT; ++t) {
+        const int task = t * per_pass + tid / tp;
+        if (task < rr) {
+          const int s = task / r, u = task - s * r;
+          const cx<T>* xs = Ts + (size_t)s * n1;
+          const cx<T>* xu = Ts + (size_t)u * n1;
+          const cx<T>* ou = Xs + (size_t)u * n1;
+          for (int i = q; i < n1; i += tp) {
+            const cx<T> a = xs[i], b = xu[i];
+            cfmaconj(a0[t], a, b);
+            cfmaconj(dd[t], a, b - ou[i]);
+            if (i + 1 < n1) cfmaconj(hh[t], a - xs[i + 1], b - xu[i + 1]);
+          }
+        }
+      }
+    }
+    for (int i0 = 0; !arrays_in_smem && i0 < n1; i0 += kGramRows) {
       const int nrow = min(kGramRows + 1, n1 - i0);
       for (int e = tid; e < r * kGramLd; e += blockDim.x) {
         const int s = e / kGramLd, ii = e - s * kGramLd;
@@ -950,11 +1016,11 @@ __host__ __device__ constexpr int ystep_cpl(int rp) { return rp <= 16 ? 2 : 1; }
 
 // TCY (precision form, r > 16): D comes as ksplit partial sums over ranges of
 // n1 from k_dcon_tc (d.Dpart) and Z~ is formed by k_zsyn_tc afterwards.
-template <typename T, int RP, bool TCY = false>
-__global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
+// XSH: X~' of the slice staged in shared memory (the compiler then sees
+// shared-memory loads in the contraction loops), else read through L1.
+template <typename T, int RP, bool TCY, bool XSH>
+__device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem) {
   constexpr int CPL = ystep_cpl(RP), TW = 32 * CPL;
-  extern __shared__ __align__(16) unsigned char smem[];
-  if (converged(d)) return;
   const int k = blockIdx.x;
   const int j0 = blockIdx.y * TW;
   const int n1 = d.n1, n2 = d.n2, r = d.r, S = d.S, rr = r * r;
@@ -966,8 +1032,8 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
   cx<T>* Gh = Dgs + rr;                         // [rr]
   cx<T>* Yn = Gh + rr;                          // [RP][TW] the new Y~' of the tile
   const cx<T>* Xg = d.Xt + (size_t)k * r * n1;
-  const cx<T>* Xs = Xg;                         // [r][n1], staged when it fits
-  if (!TCY && !d.yx_global) {
+  const cx<T>* Xs = Xg;                         // [r][n1]
+  if constexpr (XSH) {
     cx<T>* xs = Yn + RP * TW;
     for (int e = tid; e < r * n1; e += blockDim.x) xs[e] = Xg[e];
     Xs = xs;
@@ -1105,6 +1171,14 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
         zc[o] = z[h];
       }
   }
+}
+
+// XSH is chosen at launch (d.yx_global == 0 for XSH, TCY never stages).
+template <typename T, int RP, bool TCY = false, bool XSH = !TCY>
+__global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
+  ystep_impl<T, RP, TCY, XSH && !TCY>(d, smem);
 }
 
 template <typename T>

@@ -8,6 +8,11 @@
 
 namespace tc {
 
+// Static shared memory the library's kernels declare (block reductions) is at
+// most this; sizes of dynamic shared memory are checked against the opt-in
+// limit less it.
+constexpr int kStaticSmemReserve = 2048;
+
 // The dynamic shared-memory limit is an attribute of the kernel itself, shared
 // by every live context that launches it: raise it to `bytes` if it is lower,
 // never lower it (a smaller context created later must not break the launches

@@ -68,14 +68,15 @@ inline int pad_rank(int r) {
   return r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : r <= 16 ? 16 : 32;
 }
 
+// xsh: X~' of the slice staged in shared memory (r n1 fits), else read through L1
 template <typename T>
-inline YFn<T> pick_ystep(int rp) {
+inline YFn<T> pick_ystep(int rp, bool xsh = true) {
   switch (rp) {
-    case 2: return k_ystep<T, 2>;
-    case 4: return k_ystep<T, 4>;
-    case 8: return k_ystep<T, 8>;
-    case 16: return k_ystep<T, 16>;
-    default: return k_ystep<T, 32>;
+    case 2: return xsh ? k_ystep<T, 2, false, true> : k_ystep<T, 2, false, false>;
+    case 4: return xsh ? k_ystep<T, 4, false, true> : k_ystep<T, 4, false, false>;
+    case 8: return xsh ? k_ystep<T, 8, false, true> : k_ystep<T, 8, false, false>;
+    case 16: return xsh ? k_ystep<T, 16, false, true> : k_ystep<T, 16, false, false>;
+    default: return xsh ? k_ystep<T, 32, false, true> : k_ystep<T, 32, false, false>;
   }
 }
 
@@ -181,6 +182,7 @@ class Engine final : public EngineBase {
     TC_CUDA_TRY(cudaGetDevice(&device_));
     int optin = 0;
     TC_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device_));
+    optin -= kStaticSmemReserve;  // room for the kernels' static shared memory
     upload_twiddles<T>();
     TC_CUDA_TRY(cudaGetLastError());
 
@@ -254,10 +256,30 @@ class Engine final : public EngineBase {
     }
     xstep_ = pick_xstep_for<T>(rp_, mixed_);
     TC_CUDA_TRY(allow_dynamic_smem((const void*)xstep_, xstep_smem_));
-    ystep_ = pick_ystep<T>(rp_);
+    // r > 16: the X-step spread over four kernels (k_xsplit.cuh)
+    xsplit_ = rp_ == 32 && xb_smem_bytes<T>(n1_) <= (size_t)optin && xa_smem_bytes<double>(r_) <= (size_t)optin &&
+              xg_smem_bytes<T>(r_) <= (size_t)optin;
+    if (xsplit_) {
+      gch_ = (n1_ + kXgRows - 1) / kXgRows;
+      d_.gch = gch_;
+      d_.Apg = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
+      d_.Pg = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
+      d_.certA = alloc<int>((size_t)S_, err);
+      d_.tstep = alloc<T>((size_t)S_, err);
+      d_.Gpart = alloc<cx<T>>((size_t)S_ * gch_ * 3 * r_ * r_, err);
+      if (!err.empty()) return TC_ERR_NOMEM;
+      xa_smem_ = xa_smem_bytes<double>(r_);
+      xb_smem_ = xb_smem_bytes<T>(n1_);
+      xg_smem_ = xg_smem_bytes<T>(r_);
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xa<T, double>, xa_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xc<T, double>, xa_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xb<T>, xb_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xg<T>, xg_smem_));
+    }
     ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
     d_.yx_global = ystep_smem_ > (size_t)optin ? 1 : 0;
     if (d_.yx_global) ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_, false);
+    ystep_ = pick_ystep<T>(rp_, !d_.yx_global);
     qcon_ = pick_qcon<T>(rp_);
     qcon_smem_ = qcon_smem_bytes<T>(n2_, r_, rp_);
     qgrid_ = dim3(S_, (n1_ + 31) / 32);
@@ -641,6 +663,13 @@ class Engine final : public EngineBase {
   }
   void launch_qcon(cudaStream_t s) { qcon_<<<qgrid_, qthreads_, qcon_smem_, s>>>(d_, Q_); }
   void launch_xstep(cudaStream_t s) {
+    if (xsplit_) {
+      k_xa<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      k_xb<T><<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
+      k_xg<T><<<dim3(S_, gch_), 256, xg_smem_, s>>>(d_);
+      k_xc<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      return;
+    }
     xstep_<<<S_, xstep_threads(rp_), xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
   }
   void launch_ystep(cudaStream_t s) {
@@ -704,6 +733,9 @@ class Engine final : public EngineBase {
   bool slabs_in_smem_ = true;
   bool xarrays_in_smem_ = true;
   bool mixed_ = false;
+  bool xsplit_ = false;  // X-step of large ranks as four kernels
+  int gch_ = 0;
+  size_t xa_smem_ = 0, xb_smem_ = 0, xg_smem_ = 0;
   bool tcy_ = false;  // tensor-core Y-step (D partials, update, Z~ synthesis)
   TcKernels<T> tck_;
   int ksplit_ = 1;

@@ -152,6 +152,7 @@ struct GradEngine final : tc_grad {
     TCG_TRY(cudaGetDevice(&device));
     int optin = 0;
     TCG_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    optin -= kStaticSmemReserve;  // room for the kernels' static shared memory
     if constexpr (sizeof(T) == 8) fft::upload_tables<T>();
 
     T* Gint = alloc<T>(N, err);

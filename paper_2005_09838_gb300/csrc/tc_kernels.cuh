@@ -60,6 +60,13 @@ struct Dev {
   int yx_global;     // 1: k_ystep reads X~ of the slice from global memory (r n1 too large to stage)
   cx<T>* Dpart;      // [S][ksplit][r][n2] partial D = X~'^H R~ of the tensor-core Y-step
   int ksplit;
+  // X-step of large ranks spread over four kernels (k_xa, k_xb, k_xg, k_xc)
+  cx<T>* Apg;        // [S][r][r] A^+
+  cx<T>* Pg;         // [S][r][r] P = A A^+
+  int* certA;        // [S] 1 when A^+ = A^-1 (P = I)
+  T* tstep;          // [S] step t1 along d_X
+  cx<T>* Gpart;      // [S][gch][3][r][r] partial Grams over kXgRows rows
+  int gch;
 };
 
 // True once the stopping test has fired: the iteration kernels return at once.
@@ -122,5 +129,6 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
 #include "k_slab.cuh"
 #include "k_slab_f.cuh"
 #include "k_slice.cuh"
+#include "k_xsplit.cuh"
 #include "k_aux.cuh"
 #include "k_grad.cuh"

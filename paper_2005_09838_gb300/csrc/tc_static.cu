@@ -121,6 +121,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   if (s0 != TC_OK) return s0;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  optin -= kStaticSmemReserve;  // room for the kernels' static shared memory
 
   const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, mw = (n2 + 31) / 32;
   const int rp = pad_rank<T>(r);
@@ -185,7 +186,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   // ---- kernels (generic mode-3 transform) ------------------------------------------------
   SlabFn<T> slab[3];
   slab_table<T, 0>(slab);
-  YFn<T> ystep = pick_ystep<T>(rp);
+  YFn<T> ystep = pick_ystep<T>(rp, !yxg);
   QFn<T> qcon = pick_qcon<T>(rp);
   for (int m = 0; m < 3; ++m) allow_dynamic_smem((const void*)slab[m], lay.total);
   XFn<T> xstep = pick_xstep_for<T>(rp, false);
