@@ -450,6 +450,121 @@ __device__ inline void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx
   __syncthreads();
 }
 
+// The same eigendecomposition by one warp, for small r, where the block-wide
+// barriers of block_jacobi_pinv would cost more than the rotations: then A^+
+// and P = A A^+ with the cutoff rule.
+template <typename T>
+__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+                                        T rtol, T* lmax_out) {
+  const int lane = threadIdx.x & 31;
+  const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
+  const int m = (r + 1) & ~1, np = m / 2;
+  // rotation of pair k: piv[2k] = (cs, sn), piv[2k + 1] = unit phase u; rows p, q in rpq
+  int* rpq = reinterpret_cast<int*>(piv + 2 * np);  // 2 ints per pair (fits in the third r values)
+  __syncwarp();
+  for (int e = lane; e < r * r; e += 32) {
+    W[e] = A[e];
+    const int i = e / r, j = e - i * r;
+    V[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    bool any = false;
+    for (int round = 0; round < m - 1; ++round) {
+      // ---- rotations of this round (lane k < np) ----
+      bool rot = false;
+      if (lane < np) {
+        int a, b;
+        if (lane == 0) {
+          a = round;
+          b = m - 1;
+        } else {
+          a = (round + lane) % (m - 1);
+          b = (round - lane + m - 1) % (m - 1);
+        }
+        const int p = min(a, b), q = max(a, b);
+        T cs = T(1), sn = T(0);
+        cx<T> uu = {T(1), T(0)};
+        if (q < r) {
+          const cx<T> c = W[p * r + q];
+          const T n2 = c.re * c.re + c.im * c.im;
+          const T app = W[p * r + p].re, aqq = W[q * r + q].re;
+          // below 4u max(|a_pp|, |a_qq|) the entry is at the rounding level of the
+          // rotations themselves (its effect on any eigenvalue is below u^2 lambda_max)
+          const T thr = T(4) * u_round * fmax(fabs(app), fabs(aqq));
+          if (n2 > tiny_pivot<T>() && n2 > thr * thr) {
+            const T iac = rsqrt(n2);
+            uu = cx<T>{c.re * iac, c.im * iac};
+            const T tau = (aqq - app) * T(0.5) * iac;
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            cs = rsqrt(T(1) + t * t);
+            sn = t * cs;
+            rot = true;
+          }
+        }
+        piv[2 * lane] = cx<T>{cs, sn};
+        piv[2 * lane + 1] = uu;
+        rpq[2 * lane] = p;
+        rpq[2 * lane + 1] = (q < r) ? q : -1;
+      }
+      rot = __any_sync(0xffffffffu, rot);
+      __syncwarp();
+      if (!rot) continue;
+      any = true;
+      // ---- columns: W J and V J (item = row i, pair k) ----
+      for (int e = lane; e < r * np; e += 32) {
+        const int k = e / r, i = e - k * r;
+        const int p = rpq[2 * k], q = rpq[2 * k + 1];
+        if (q < 0) continue;
+        const T cs = piv[2 * k].re, sn = piv[2 * k].im;
+        const cx<T> uu = piv[2 * k + 1];
+        // J = [[cs, sn u], [-sn conj(u), cs]] on columns p, q
+        const cx<T> aip = W[i * r + p], aiq = W[i * r + q];
+        W[i * r + p] = aip * cs - cmulc(aiq, uu) * sn;
+        W[i * r + q] = cmul(aip, uu) * sn + aiq * cs;
+        const cx<T> vip = V[i * r + p], viq = V[i * r + q];
+        V[i * r + p] = vip * cs - cmulc(viq, uu) * sn;
+        V[i * r + q] = cmul(vip, uu) * sn + viq * cs;
+      }
+      __syncwarp();
+      // ---- rows: J^H (W J) (item = pair k, column j) ----
+      for (int e = lane; e < r * np; e += 32) {
+        const int k = e / r, j = e - k * r;
+        const int p = rpq[2 * k], q = rpq[2 * k + 1];
+        if (q < 0) continue;
+        const T cs = piv[2 * k].re, sn = piv[2 * k].im;
+        const cx<T> uu = piv[2 * k + 1];
+        const cx<T> apj = W[p * r + j], aqj = W[q * r + j];
+        W[p * r + j] = apj * cs - cmul(aqj, uu) * sn;
+        W[q * r + j] = cmulc(apj, uu) * sn + aqj * cs;
+      }
+      __syncwarp();
+    }
+    if (!any) break;
+  }
+  // eigenvalues on the diagonal; cutoff relative to lambda_max
+  T lmax = T(0);
+  for (int i = 0; i < r; ++i) lmax = fmax(lmax, W[i * r + i].re);
+  const T cut = rtol * lmax;
+  if (lane == 0) *lmax_out = lmax;
+  __syncwarp();
+  for (int e = lane; e < r * r; e += 32) {
+    const int i = e / r, j = e - i * r;
+    cx<T> sa = {T(0), T(0)}, sp = {T(0), T(0)};
+    for (int mm = 0; mm < r; ++mm) {
+      const T lam = W[mm * r + mm].re;
+      if (lmax > T(0) && lam > cut) {
+        const cx<T> vv = cmulc(V[i * r + mm], V[j * r + mm]);  // V_im conj(V_jm)
+        sa = sa + vv * (T(1) / lam);
+        sp = sp + vv;
+      }
+    }
+    Ap[e] = sa;
+    P[e] = sp;
+  }
+  __syncwarp();
+}
+
 // The eigendecomposition fallback of block_pinv_herm.  For the FP64-storage
 // solves of an FP32 engine (DF) it runs in FP32 on the FP32 pipes (the FP64
 // pipe of this part is 1/64 of it), with the cutoff raised to at least
@@ -458,6 +573,7 @@ __device__ inline void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx
 template <typename TS, bool DF>
 __device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
                                        int r, TS rtol, TS* lmax_out) {
+  const bool small = r <= 16;  // one warp; the other threads wait at the caller's barrier
   if constexpr (DF && sizeof(TS) == 8) {
     const int tid = threadIdx.x, nt = blockDim.x, rr = r * r;
     cx<float>* Af = reinterpret_cast<cx<float>*>(W);  // W holds 4 r^2 float pairs
@@ -470,12 +586,20 @@ __device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, c
     for (int e = tid; e < rr; e += nt) Af[e] = cx<float>{(float)A[e].re, (float)A[e].im};
     __syncthreads();
     const float rt = fmaxf((float)rtol, (float)r * 1.1920929e-7f);
-    block_jacobi_pinv<float>(Af, Apf, Pf, Vf, Wf, pivf, r, rt, lmf);
+    if (small) {
+      if (tid < 32) warp_jacobi_pinv<float>(Af, Apf, Pf, Vf, Wf, pivf, r, rt, lmf);
+      __syncthreads();
+    } else {
+      block_jacobi_pinv<float>(Af, Apf, Pf, Vf, Wf, pivf, r, rt, lmf);
+    }
     for (int e = tid; e < rr; e += nt) {
       Ap[e] = cx<TS>{(TS)Apf[e].re, (TS)Apf[e].im};
       P[e] = cx<TS>{(TS)Pf[e].re, (TS)Pf[e].im};
     }
     if (tid == 0) *lmax_out = (TS)*lmf;
+    __syncthreads();
+  } else if (small) {
+    if (threadIdx.x < 32) warp_jacobi_pinv<TS>(A, Ap, P, V, W, piv, r, rtol, lmax_out);
     __syncthreads();
   } else {
     block_jacobi_pinv<TS>(A, Ap, P, V, W, piv, r, rtol, lmax_out);

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(kXaThreads) k_xa(Dev<T> d) {
 }
 
 // ---- B, d_X = H_rho1^{-1} B and X~' per column ----------------------------------------
+// One CTA per 8 columns, Q read through L1 (n1 too large for k_xb1).
 template <typename T>
 __global__ void __launch_bounds__(256) k_xb(Dev<T> d, const cx<T>* __restrict__ Qin) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -137,6 +138,89 @@ __global__ void __launch_bounds__(256) k_xb(Dev<T> d, const cx<T>* __restrict__ 
       cx<T> v = d.scaled ? x0 + col[i] * t1 : x0 + col[i];
       if (realslice) v.im = T(0);
       Xp[i] = v;
+      if (d.conv) dmax = fmax(dmax, (double)cabs(v - x0));
+    }
+  }
+  if (d.conv) block_max_to(dmax, d.conv + 0);
+}
+
+// ---- the same per slice: one CTA of 1024 threads, warp s forms column s ---------------
+// Q of the slice is staged once; each warp writes its column of B to the
+// slice's work array (L2-resident) and, once every warp has read Q, copies it
+// back into its own row of the staged Q for the tridiagonal solve.
+
+template <typename T>
+__host__ __device__ inline size_t xb1_smem_bytes(int n1, int r) {
+  return align_up(2 * (size_t)n1 * sizeof(T), 16) + (2 * 32 * 32 + (size_t)r * n1) * sizeof(cx<T>);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_xb1(Dev<T> d, const cx<T>* __restrict__ Qin) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
+  const int k = blockIdx.x, n1 = d.n1, r = d.r, rr = r * r;
+  const int tid = threadIdx.x, lane = tid & 31, s = tid >> 5;
+  T* hinv = reinterpret_cast<T*>(smem);
+  T* ha = hinv + n1;
+  cx<T>* apc = reinterpret_cast<cx<T>*>(smem + align_up(2 * (size_t)n1 * sizeof(T), 16));  // [32][32]
+  cx<T>* pc = apc + 32 * 32;
+  cx<T>* qs = pc + 32 * 32;  // [r][n1]
+  for (int i = tid; i < 2 * n1; i += blockDim.x) hinv[i] = d.hinv[i];
+  if (s < r) {
+    apc[s * 32 + lane] = lane < r ? d.Apg[(size_t)k * rr + lane * r + s] : cx<T>{T(0), T(0)};
+    pc[s * 32 + lane] = lane < r ? d.Pg[(size_t)k * rr + lane * r + s] : cx<T>{T(0), T(0)};
+  }
+  {
+    const cx<T>* Qk = Qin + (size_t)k * r * n1;
+    const int nq = r * n1, nt = blockDim.x;
+    int e = tid;
+    for (; e + 3 * nt < nq; e += 4 * nt) {
+      cx<T> v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = ldg_cx(Qk + e + q * nt);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) qs[e + q * nt] = v[q];
+    }
+    for (; e < nq; e += nt) qs[e] = ldg_cx(Qk + e);
+  }
+  __syncthreads();
+  const bool realslice = (k == 0) || (2 * k == d.n3);
+  const T rho1 = d.rho1;
+  const cx<T>* X = d.Xt + (size_t)k * r * n1;
+  cx<T>* Bw = d.Tb + (size_t)k * r * n1 + (size_t)s * n1;  // column s of B, then of X~'
+  if (s < r) {
+    const bool certA = d.certA[k] != 0;
+    const cx<T>* ap = apc + s * 32;
+    const cx<T>* pp = pc + s * 32;
+    for (int i = lane; i < n1; i += 32) {
+      cx<T> acc = {T(0), T(0)};
+      for (int u = 0; u < r; ++u) cfma(acc, qs[(size_t)u * n1 + i], ap[u]);
+      if (rho1 != T(0)) {
+        cx<T> hx = {T(0), T(0)};
+        if (certA) {
+          hx = hth_at(X + (size_t)s * n1, i, n1);  // P = I
+        } else {
+          for (int u = 0; u < r; ++u) cfma(hx, hth_at(X + (size_t)u * n1, i, n1), pp[u]);
+        }
+        acc = acc - hx * rho1;
+      }
+      Bw[i] = acc;
+    }
+  }
+  __syncthreads();  // every warp has read Q (and its own B stores are visible to it)
+  double dmax = 0.0;
+  if (s < r) {
+    cx<T>* col = qs + (size_t)s * n1;
+    for (int i = lane; i < n1; i += 32) col[i] = Bw[i];
+    __syncwarp();
+    if (rho1 != T(0) && n1 > 1) warp_tridiag_solve<T>(col, n1, hinv, ha);
+    __syncwarp();
+    const T t1 = d.tstep[k];
+    for (int i = lane; i < n1; i += 32) {
+      const cx<T> x0 = X[(size_t)s * n1 + i];
+      cx<T> v = d.scaled ? x0 + col[i] * t1 : x0 + col[i];
+      if (realslice) v.im = T(0);
+      Bw[i] = v;
       if (d.conv) dmax = fmax(dmax, (double)cabs(v - x0));
     }
   }

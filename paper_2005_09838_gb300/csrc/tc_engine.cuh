@@ -62,6 +62,8 @@ template <typename T>
 using YFn = void (*)(Dev<T>);
 template <typename T>
 using QFn = void (*)(Dev<T>, cx<T>*);
+template <typename T>
+using XbFn = void (*)(Dev<T>, const cx<T>*);
 
 template <typename T>
 inline int pad_rank(int r) {
@@ -163,6 +165,12 @@ class Engine final : public EngineBase {
     graph_exec_ = nullptr;
     if (cap_stream_) cudaStreamDestroy(cap_stream_);
     cap_stream_ = nullptr;
+    if (aux_stream_) cudaStreamDestroy(aux_stream_);
+    aux_stream_ = nullptr;
+    for (cudaEvent_t* e : {&ev_fork_, &ev_join_}) {
+      if (*e) cudaEventDestroy(*e);
+      *e = nullptr;
+    }
     for (void* p : allocs_) cudaFree(p);
     allocs_.clear();
   }
@@ -269,11 +277,14 @@ class Engine final : public EngineBase {
       d_.Gpart = alloc<cx<T>>((size_t)S_ * gch_ * 3 * r_ * r_, err);
       if (!err.empty()) return TC_ERR_NOMEM;
       xa_smem_ = xa_smem_bytes<double>(r_);
-      xb_smem_ = xb_smem_bytes<T>(n1_);
+      // one CTA per slice when its Q fits in shared memory, else a CTA per 8 columns
+      xb_slice_ = xb1_smem_bytes<T>(n1_, r_) <= (size_t)optin;
+      xb_smem_ = xb_slice_ ? xb1_smem_bytes<T>(n1_, r_) : xb_smem_bytes<T>(n1_);
+      xb_ = xb_slice_ ? k_xb1<T> : k_xb<T>;
       xg_smem_ = xg_smem_bytes<T>(r_);
       TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xa<T, double>, xa_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xc<T, double>, xa_smem_));
-      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xb<T>, xb_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)xb_, xb_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xg<T>, xg_smem_));
     }
     ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
@@ -567,13 +578,35 @@ class Engine final : public EngineBase {
       err = std::string("pending error before graph capture: ") + cudaGetErrorString(pre);
       return TC_ERR_CUDA;
     }
+    if (xsplit_ && !aux_stream_) {
+      TC_CUDA_TRY(cudaStreamCreateWithFlags(&aux_stream_, cudaStreamNonBlocking));
+      TC_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+      TC_CUDA_TRY(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
+    }
     TC_CUDA_TRY(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
     const char* at = "qcon";
-    launch_qcon(cap_stream_);
-    cudaError_t le = cudaPeekAtLastError();
+    cudaError_t le = cudaSuccess;
+    if (xsplit_) {
+      // A^+ (k_xa) needs only the tile Grams of the previous Y-step: a branch of
+      // the graph that runs beside the Q contraction
+      le = cudaEventRecord(ev_fork_, cap_stream_);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(aux_stream_, ev_fork_, 0);
+      if (le == cudaSuccess) {
+        at = "xa";
+        k_xa<T, double><<<S_, kXaThreads, xa_smem_, aux_stream_>>>(d_);
+        le = cudaPeekAtLastError();
+      }
+      if (le == cudaSuccess) le = cudaEventRecord(ev_join_, aux_stream_);
+    }
+    if (le == cudaSuccess) {
+      at = "qcon";
+      launch_qcon(cap_stream_);
+      le = cudaPeekAtLastError();
+    }
+    if (le == cudaSuccess && xsplit_) le = cudaStreamWaitEvent(cap_stream_, ev_join_, 0);
     if (le == cudaSuccess) {
       at = "xstep";
-      launch_xstep(cap_stream_);
+      launch_xstep(cap_stream_, xsplit_);
       le = cudaPeekAtLastError();
     }
     if (le == cudaSuccess) {
@@ -662,10 +695,12 @@ class Engine final : public EngineBase {
     slab_[mode]<<<n1_, slab_threads_, slab_smem_, s>>>(d_, Wout, slabs_in_smem_ ? 1 : 0, init);
   }
   void launch_qcon(cudaStream_t s) { qcon_<<<qgrid_, qthreads_, qcon_smem_, s>>>(d_, Q_); }
-  void launch_xstep(cudaStream_t s) {
+  // skip_xa: k_xa was launched on a branch of its own (graph capture)
+  void launch_xstep(cudaStream_t s, bool skip_xa = false) {
     if (xsplit_) {
-      k_xa<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
-      k_xb<T><<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
+      if (!skip_xa) k_xa<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      if (xb_slice_) xb_<<<S_, 1024, xb_smem_, s>>>(d_, Q_);
+      else xb_<<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
       k_xg<T><<<dim3(S_, gch_), 256, xg_smem_, s>>>(d_);
       k_xc<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
       return;
@@ -736,6 +771,10 @@ class Engine final : public EngineBase {
   bool xsplit_ = false;  // X-step of large ranks as four kernels
   int gch_ = 0;
   size_t xa_smem_ = 0, xb_smem_ = 0, xg_smem_ = 0;
+  bool xb_slice_ = false;
+  cudaStream_t aux_stream_ = nullptr;  // graph branch of k_xa during capture
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
+  XbFn<T> xb_ = nullptr;
   bool tcy_ = false;  // tensor-core Y-step (D partials, update, Z~ synthesis)
   TcKernels<T> tck_;
   int ksplit_ = 1;

@@ -177,6 +177,17 @@ def test_c2_full_size_three_iterations_fp32():
     assert abs(got["f0"] - ref["f0"]) <= TOL["fp32"] * abs(ref["f0"])
 
 
+@pytest.mark.parametrize("precision,n1", [("fp32", 1000), ("fp64", 700)])
+def test_rank32_longest_slices(precision, n1):
+    # r = 32 with the slice's Q too large for one CTA's shared memory: the
+    # X-step forms B with one CTA per 8 columns (FP32: Q staged per CTA; FP64:
+    # read through L1)
+    w = wl.custom(n1, 40, 8, 32, 0.3, seed=3200 + n1, iters=6)
+    inst, ref, got = _run_pair(w, "R", precision, w.iters)
+    assert _rel(got["W"], ref["W"]) <= TOL[precision]
+    assert abs(got["f0"] - ref["f0"]) <= TOL[precision] * abs(ref["f0"])
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_rank32_long_slices(precision):
     # r = 32 (block Gauss-Jordan pseudo-inverse) with n1 = 529: the FP32 Y-step
