@@ -1226,8 +1226,19 @@ __device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem)
     const int s = e / TW, c = e - s * TW;
     cx<T> v = {T(0), T(0)};
     if constexpr (TCY) {
-      if (j0 + c < n2)
-        for (int z = 0; z < d.ksplit; ++z) v = v + d.Dpart[(((size_t)k * d.ksplit + z) * r + s) * n2 + j0 + c];
+      if (j0 + c < n2) {
+        const cx<T>* dp = d.Dpart + ((size_t)k * d.ksplit * r + s) * n2 + j0 + c;  // + z r n2
+        const size_t zs = (size_t)r * n2;
+        int z = 0;
+        for (; z + 4 <= d.ksplit; z += 4) {  // four loads in flight, summed in order
+          cx<T> q[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) q[w] = dp[(z + w) * zs];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) v = v + q[w];
+        }
+        for (; z < d.ksplit; ++z) v = v + dp[z * zs];
+      }
     } else {
       for (int w = 0; w < nw; ++w) v = v + red[(w * RP + s) * TW + c];
     }
@@ -1254,18 +1265,24 @@ __device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem)
   __syncthreads();
 
   // ---- Grams of the new Y~' over each 32 columns (A of the next X-step) ----------------
+  // a thread per (s, u) pair of a tile; the columns are visited from (u mod 32)
+  // on, so the threads of a half-warp (consecutive u) read different banks
   const int ntask = r * (r + 1) / 2;
-  for (int t = wid; t < CPL * ntask; t += nw) {
+  for (int t = tid; t < CPL * ntask; t += blockDim.x) {
     const int h = t / ntask, task = t - h * ntask;
     const int tile = blockIdx.y * CPL + h;
     if (tile >= d.ytiles) continue;
     int s, u;
     tri_index(task, r, s, u);
+    const cx<T>* ys = Yn + s * TW + 32 * h;
+    const cx<T>* yu = Yn + u * TW + 32 * h;
     cx<T> g = {T(0), T(0)};
-    cfmac(g, Yn[s * TW + 32 * h + lane], Yn[u * TW + 32 * h + lane]);
-    g.re = warp_sum(g.re);
-    g.im = warp_sum(g.im);
-    if (lane == 0) d.Ag[((size_t)k * d.ytiles + tile) * ntask + task] = cx<double>{(double)g.re, (double)g.im};
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {
+      const int cc = (c + u) & 31;
+      cfmac(g, ys[cc], yu[cc]);
+    }
+    d.Ag[((size_t)k * d.ytiles + tile) * ntask + task] = cx<double>{(double)g.re, (double)g.im};
   }
 
   // ---- Z~(:, tile, k) = X~' Y~'  (step 3, written for the slab kernel) ----------------

@@ -21,6 +21,7 @@ CASES = [  # precision, shape, r, observed
     ("fp64", (9, 30, 12), 3, 0.4),
     ("fp32", (30, 50, 28), 5, 0.3),
     ("fp32", (12, 24, 8), 3, 0.6),
+    ("tf32", (200, 96, 12), 32, 0.3),   # tensor cores, the X-step's graph branch
 ]
 
 
@@ -38,9 +39,10 @@ def _ctx(precision, shape, r, obs, seed):
     w = wl.custom(*shape, r, obs, seed=seed)
     inst = wl.generate(w)
     dt = np.float64 if precision == "fp64" else np.float32
-    if precision == "fp32":
+    if precision != "fp64":
         inst = wl.as_precision(inst, np.float32)
-    p = tc.make_params(*shape, r, *SETTING, precision=tc.TC_FP64 if precision == "fp64" else tc.TC_FP32)
+    prec = {"fp64": tc.TC_FP64, "fp32": tc.TC_FP32, "tf32": tc.TC_TF32}[precision]
+    p = tc.make_params(*shape, r, *SETTING, precision=prec)
     c = tc.Completion(p, wl.to_colmajor(inst["G"], dt), wl.to_colmajor(inst["mask"], np.uint8),
                       wl.to_colmajor(inst["Y0"], dt))
     return c, inst

@@ -17,7 +17,7 @@ from oracle import method as O
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "tf32": 1e-3}
 SETTING = (1e-3, 1e-3, 1e-1)
 
 
@@ -36,13 +36,14 @@ def _rel(a, b):
 
 def _inst(w, precision):
     inst = wl.generate(w)
-    return wl.as_precision(inst, np.float32) if precision == "fp32" else inst
+    return inst if precision == "fp64" else wl.as_precision(inst, np.float32)
 
 
 @pytest.mark.parametrize("precision,shape,r,obs,iters", [
     ("fp64", (16, 48, 7), 2, 0.5, 40),      # the 16x48x7 workload (register FFT, n3 = 7)
     ("fp32", (20, 40, 112), 4, 0.3, 25),    # shared-memory transform, n3 = 112
     ("fp64", (9, 30, 12), 3, 0.4, 25),      # generic transform
+    ("tf32", (200, 96, 12), 32, 0.3, 12),   # precision form: lambda_max from the block Jacobi
 ])
 @pytest.mark.parametrize("alpha,beta", [(1.0, 1.0), (0.6, 0.8)])
 def test_scaled_steps_match_oracle(precision, shape, r, obs, iters, alpha, beta):
@@ -52,7 +53,7 @@ def test_scaled_steps_match_oracle(precision, shape, r, obs, iters, alpha, beta)
     from paper_2005_09838_gb300 import api
     w = wl.custom(*shape, r, obs, seed=4100 + shape[2])
     inst = _inst(w, precision)
-    dt = np.float32 if precision == "fp32" else np.float64
+    dt = np.float64 if precision == "fp64" else np.float32
     X0 = np.random.default_rng(4100 + shape[0]).standard_normal((shape[0], r, shape[2])).astype(dt)
     ref = O.tctf2r(inst["G"], inst["mask"], r, *SETTING, inst["Y0"], X0=X0, iters=iters, step="scaled",
                    alpha=alpha, beta=beta)
@@ -91,6 +92,7 @@ def _eps_between(hist, lo=4, margin=1.5):
     ("fp32", (20, 40, 112), 4, 0.3),
     ("fp32", (24, 36, 168), 4, 0.3),
     ("fp64", (9, 30, 12), 3, 0.4),
+    ("tf32", (200, 96, 12), 32, 0.3),   # precision form: changes from the tensor-core Z~ and split X-step
 ])
 def test_stopping_test_stops_at_the_oracle_iteration(precision, shape, r, obs):
     from paper_2005_09838_gb300 import api
