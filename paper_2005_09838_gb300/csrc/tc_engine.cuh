@@ -265,8 +265,14 @@ class Engine final : public EngineBase {
     xstep_ = pick_xstep_for<T>(rp_, mixed_);
     TC_CUDA_TRY(allow_dynamic_smem((const void*)xstep_, xstep_smem_));
     // r > 16: the X-step spread over four kernels (k_xsplit.cuh)
-    xsplit_ = rp_ == 32 && xb_smem_bytes<T>(n1_) <= (size_t)optin && xa_smem_bytes<double>(r_) <= (size_t)optin &&
-              xg_smem_bytes<T>(r_) <= (size_t)optin;
+    // the X-step as four kernels (k_xsplit.cuh) for r > 8 in FP32 engines and
+    // r > 16 in the FP64 engine; below that one CTA per slice is faster (the
+    // r x r work is small and the extra launches and barriers dominate: 35 us
+    // against 49 us for the 144 x 288 x 168, r = 8 workload)
+    const bool s64 = solve64<T>(rp_, mixed_);
+    const size_t xa_bytes = s64 ? xa_smem_bytes<double>(r_) : xa_smem_bytes<T>(r_);
+    xsplit_ = (sizeof(T) == 4 ? rp_ >= 16 : rp_ == 32) && xb_smem_bytes<T>(n1_) <= (size_t)optin &&
+              xa_bytes <= (size_t)optin && xg_smem_bytes<T>(r_) <= (size_t)optin;
     if (xsplit_) {
       gch_ = (n1_ + kXgRows - 1) / kXgRows;
       d_.gch = gch_;
@@ -276,14 +282,16 @@ class Engine final : public EngineBase {
       d_.tstep = alloc<T>((size_t)S_, err);
       d_.Gpart = alloc<cx<T>>((size_t)S_ * gch_ * 3 * r_ * r_, err);
       if (!err.empty()) return TC_ERR_NOMEM;
-      xa_smem_ = xa_smem_bytes<double>(r_);
+      xa_smem_ = xa_bytes;
+      xa_fn_ = s64 ? k_xa<T, double> : k_xa<T, T>;
+      xc_fn_ = s64 ? k_xc<T, double> : k_xc<T, T>;
       // one CTA per slice when its Q fits in shared memory, else a CTA per 8 columns
       xb_slice_ = xb1_smem_bytes<T>(n1_, r_) <= (size_t)optin;
       xb_smem_ = xb_slice_ ? xb1_smem_bytes<T>(n1_, r_) : xb_smem_bytes<T>(n1_);
       xb_ = xb_slice_ ? k_xb1<T> : k_xb<T>;
       xg_smem_ = xg_smem_bytes<T>(r_);
-      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xa<T, double>, xa_smem_));
-      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xc<T, double>, xa_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)xa_fn_, xa_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)xc_fn_, xa_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)xb_, xb_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xg<T>, xg_smem_));
     }
@@ -593,7 +601,7 @@ class Engine final : public EngineBase {
       if (le == cudaSuccess) le = cudaStreamWaitEvent(aux_stream_, ev_fork_, 0);
       if (le == cudaSuccess) {
         at = "xa";
-        k_xa<T, double><<<S_, kXaThreads, xa_smem_, aux_stream_>>>(d_);
+        xa_fn_<<<S_, kXaThreads, xa_smem_, aux_stream_>>>(d_);
         le = cudaPeekAtLastError();
       }
       if (le == cudaSuccess) le = cudaEventRecord(ev_join_, aux_stream_);
@@ -698,11 +706,11 @@ class Engine final : public EngineBase {
   // skip_xa: k_xa was launched on a branch of its own (graph capture)
   void launch_xstep(cudaStream_t s, bool skip_xa = false) {
     if (xsplit_) {
-      if (!skip_xa) k_xa<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      if (!skip_xa) xa_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
       if (xb_slice_) xb_<<<S_, 1024, xb_smem_, s>>>(d_, Q_);
       else xb_<<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
       k_xg<T><<<dim3(S_, gch_), 256, xg_smem_, s>>>(d_);
-      k_xc<T, double><<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      xc_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
       return;
     }
     xstep_<<<S_, xstep_threads(rp_), xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
@@ -768,7 +776,8 @@ class Engine final : public EngineBase {
   bool slabs_in_smem_ = true;
   bool xarrays_in_smem_ = true;
   bool mixed_ = false;
-  bool xsplit_ = false;  // X-step of large ranks as four kernels
+  bool xsplit_ = false;  // X-step as four kernels
+  YFn<T> xa_fn_ = nullptr, xc_fn_ = nullptr;
   int gch_ = 0;
   size_t xa_smem_ = 0, xb_smem_ = 0, xg_smem_ = 0;
   bool xb_slice_ = false;

@@ -52,8 +52,10 @@ def test_static_entry_matches_allocating_path_twice(precision):
     from paper_2005_09838_gb300 import tc
     prec = tc.TC_FP64 if precision == "fp64" else tc.TC_FP32
     stream = torch.cuda.current_stream().cuda_stream
-    cases = [((16, 48, 7), 2, 0.5, 901), ((12, 40, 12), 3, 0.3, 902)]
-    for shape, r, obs, seed in cases:  # two calls in a row, different sizes and data
+    # the third case has r > 16: the entry point's one-CTA-per-slice X-step with
+    # FP64-storage solves, against the engine's four-kernel X-step
+    cases = [((16, 48, 7), 2, 0.5, 901), ((12, 40, 12), 3, 0.3, 902), ((60, 40, 8), 20, 0.4, 903)]
+    for shape, r, obs, seed in cases:  # calls in a row, different sizes and data
         w, inst, dt = _case(shape, r, obs, seed, precision)
         p = tc.make_params(w.n1, w.n2, w.n3, w.r, 1e-3, 1e-3, 1e-1, precision=prec)
         g = wl.to_colmajor(inst["G"], dt)
