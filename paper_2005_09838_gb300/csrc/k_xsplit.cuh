@@ -290,11 +290,13 @@ __global__ void __launch_bounds__(256) k_xg(Dev<T> d) {
     }
     return;
   }
-  // a thread takes a 2 x 2 block of (s, u) pairs: 10 loads per row feed 12 products
+  // a thread takes the pairs {s0, s0 + rb} x {u0, u0 + rb} (rb = ceil(r / 2)):
+  // 10 loads per row feed 12 products, and consecutive threads (consecutive
+  // u0) read consecutive rows of odd pitch, so a half-warp hits distinct banks
   const int rb = (r + 1) / 2;
   for (int blk = tid; blk < rb * rb; blk += blockDim.x) {
-    const int s0 = 2 * (blk / rb), u0 = 2 * (blk % rb);
-    const int s1 = min(s0 + 1, r - 1), u1 = min(u0 + 1, r - 1);
+    const int s0 = blk / rb, u0 = blk % rb;
+    const int s1 = min(s0 + rb, r - 1), u1 = min(u0 + rb, r - 1);
     const cx<T>* xs[2] = {gx + s0 * kXgLd, gx + s1 * kXgLd};
     const cx<T>* xu[2] = {gx + u0 * kXgLd, gx + u1 * kXgLd};
     const cx<T>* ou[2] = {go + u0 * kXgLd, go + u1 * kXgLd};
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(256) k_xg(Dev<T> d) {
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int y = 0; y < 2; ++y) {
-        const int s = s0 + x, u = u0 + y;
+        const int s = s0 + x * rb, u = u0 + y * rb;
         if (s < r && u < r) {
           const int task = s * r + u;
           out[task] = a0[x][y];
