@@ -92,6 +92,8 @@ __device__ __forceinline__ int gauss_jordan_inplace(cx<T>* W, cx<T>* piv, int r,
     return cx<T>{ok ? rcp_refined(pv) : T(0), ok ? T(1) : T(0)};
   };
   if (t == 0) piv[0] = pivot_info(W[0].re);
+  const bool one = rr <= nt;  // each thread owns at most one element: its (i, j) once
+  const int ti = t / r, tj = t - ti * r;
   sync();
   for (int p = 0; p < r; ++p) {
     const cx<T>* src = W + (p & 1) * rr;
@@ -99,14 +101,18 @@ __device__ __forceinline__ int gauss_jordan_inplace(cx<T>* W, cx<T>* piv, int r,
     const cx<T> pinfo = piv[p & 1];
     if (pinfo.im == T(0)) return 0;
     const T ip = pinfo.re;
-    for (int e = t; e < rr; e += nt) {
-      const int i = e / r, j = e - i * r;
+    auto step = [&](int e, int i, int j) {
       cx<T> v;
       if (i == p) v = (j == p) ? cx<T>{ip, T(0)} : src[p * r + j] * ip;
       else if (j == p) v = src[i * r + p] * (-ip);
       else v = src[e] - cmul(src[i * r + p], src[p * r + j] * ip);
       dst[e] = v;
       if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = pivot_info(v.re);
+    };
+    if (one) {
+      if (t < rr) step(t, ti, tj);
+    } else {
+      for (int e = t; e < rr; e += nt) step(e, e / r, e % r);
     }
     sync();
   }
@@ -179,6 +185,8 @@ __device__ __forceinline__ int gauss_jordan_inplace_df(cx<double>* W64, cx<doubl
     const cx<double> v = W64[e];
     W[e] = dfc{df_from(v.re), df_from(v.im)};
   }
+  const bool one = rr <= nt;  // each thread owns at most one element: its (i, j) once
+  const int ti = t / r, tj = t - ti * r;
   sync();
   int ok = 1;
   for (int p = 0; p < r; ++p) {
@@ -190,14 +198,18 @@ __device__ __forceinline__ int gauss_jordan_inplace_df(cx<double>* W64, cx<doubl
       break;
     }
     const df ip = pinfo.re, nip = df_neg(ip);
-    for (int e = t; e < rr; e += nt) {
-      const int i = e / r, j = e - i * r;
+    auto step = [&](int e, int i, int j) {
       dfc v;
       if (i == p) v = (j == p) ? dfc{ip, df{0.f, 0.f}} : dfc_scale(src[p * r + j], ip);
       else if (j == p) v = dfc_scale(src[i * r + p], nip);
       else v = dfc_sub(src[e], dfc_mul(src[i * r + p], dfc_scale(src[p * r + j], ip)));
       dst[e] = v;
       if (i == p + 1 && j == p + 1) pv2[(p + 1) & 1] = pivot_info(v.re);
+    };
+    if (one) {
+      if (t < rr) step(t, ti, tj);
+    } else {
+      for (int e = t; e < rr; e += nt) step(e, e / r, e % r);
     }
     sync();
   }

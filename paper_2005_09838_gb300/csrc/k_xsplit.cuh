@@ -218,13 +218,22 @@ __global__ void __launch_bounds__(1024, 1) k_xb1(Dev<T> d, const cx<T>* __restri
     if (rho1 != T(0) && n1 > 1) warp_tridiag_solve<T>(col, n1, hinv, ha);
     __syncwarp();
     const T t1 = d.tstep[k];
-    for (int i = lane; i < n1; i += 32) {
-      const cx<T> x0 = X[(size_t)s * n1 + i];
+    const cx<T>* xs = X + (size_t)s * n1;
+    auto update = [&](int i, cx<T> x0) {
       cx<T> v = d.scaled ? x0 + col[i] * t1 : x0 + col[i];
       if (realslice) v.im = T(0);
       Bw[i] = v;
       if (d.conv) dmax = fmax(dmax, (double)cabs(v - x0));
+    };
+    int i = lane;
+    for (; i + 96 < n1; i += 128) {  // four loads in flight per lane
+      cx<T> x0[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x0[q] = xs[i + 32 * q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) update(i + 32 * q, x0[q]);
     }
+    for (; i < n1; i += 32) update(i, xs[i]);
   }
   if (d.conv) block_max_to(dmax, d.conv + 0);
 }
@@ -346,19 +355,29 @@ __global__ void __launch_bounds__(256) k_xg(Dev<T> d) {
 __device__ __forceinline__ void sum_partials(const cx<float>* part, int rr, int gch, int task, bool realslice,
                                              cx<double>& a0, cx<double>& hh, cx<double>& dd) {
   df s[6] = {};
-  for (int c = 0; c < gch; ++c) {
-    const cx<float>* pc = part + (size_t)c * 3 * rr;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const cx<float> v = pc[q * rr + task];
-      if (realslice) {
-        s[2 * q] = df_add(s[2 * q], df_norm(v.re, v.im));
-      } else {
-        s[2 * q] = df_add(s[2 * q], df{v.re, 0.f});
-        s[2 * q + 1] = df_add(s[2 * q + 1], df{v.im, 0.f});
-      }
+  auto add = [&](int q, cx<float> v) {
+    if (realslice) {
+      s[2 * q] = df_add(s[2 * q], df_norm(v.re, v.im));
+    } else {
+      s[2 * q] = df_add(s[2 * q], df{v.re, 0.f});
+      s[2 * q + 1] = df_add(s[2 * q + 1], df{v.im, 0.f});
     }
+  };
+  int c = 0;
+  for (; c + 2 <= gch; c += 2) {  // six loads in flight, added in chunk order
+    cx<float> v[2][3];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[w][q] = part[((size_t)(c + w) * 3 + q) * rr + task];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) add(q, v[w][q]);
   }
+  for (; c < gch; ++c)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) add(q, part[((size_t)c * 3 + q) * rr + task]);
   a0 = cx<double>{df_to(s[0]), df_to(s[1])};
   hh = cx<double>{df_to(s[2]), df_to(s[3])};
   dd = cx<double>{df_to(s[4]), df_to(s[5])};
@@ -422,7 +441,16 @@ __global__ void __launch_bounds__(kXaThreads) k_xc(Dev<T> d) {
   }
   const cx<T>* Xp = d.Tb + (size_t)k * r * n1;
   cx<T>* X = d.Xt + (size_t)k * r * n1;
-  for (int e = tid; e < r * n1; e += blockDim.x) X[e] = Xp[e];
+  const int nx = r * n1, nt = blockDim.x;
+  int e = tid;
+  for (; e + 3 * nt < nx; e += 4 * nt) {  // four loads in flight per thread
+    cx<T> v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = Xp[e + q * nt];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[e + q * nt] = v[q];
+  }
+  for (; e < nx; e += nt) X[e] = Xp[e];
 }
 
 }  // namespace tc
