@@ -2,7 +2,9 @@
 // for a whole X-step (k_xstep) leaves most SMs idle and runs r^2 n1 Gram
 // products on one SM.  Here the same step (Eq. (updataXYW1) with the gradients
 // of Eq. (hkXYDer), formed as in k_xstep) is four kernels:
-//   k_xa   (S CTAs)               A = Y~Y~^H from the tile Grams, A^+, P, step t1
+//   k_xa   (S CTAs)               A = Y~Y~^H from the tile Grams, A^+, P, step t1; run
+//                                 after every change of Y~ (initialisation, each
+//                                 Y-step), beside the rest of that iteration
 //   k_xb1  (S CTAs) or            one warp per column s: B = Q A^+ - rho1 (H^T H X~) P,
 //   k_xb   (S x ceil(r/8) CTAs)   d_X = H_rho1^{-1} B, X~' = X~ + t1 d_X (to d.Tb); k_xb1
 //                                 stages the slice's Q in shared memory, k_xb (n1 too

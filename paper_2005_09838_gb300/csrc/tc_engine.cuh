@@ -435,6 +435,7 @@ class Engine final : public EngineBase {
     }
     k_synth_init<T><<<fgrid, 256, 0, stream_>>>(d_);                    // Z~0 = X~0 Y~0
     k_gram_tiles<T><<<dim3(S_, ytiles), 256, 0, stream_>>>(d_);         // A of the first X-step
+    if (xsplit_) xa_fn_<<<S_, kXaThreads, xa_smem_, stream_>>>(d_);     // its A^+
     launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - Z0)
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(stream_);
@@ -593,33 +594,20 @@ class Engine final : public EngineBase {
     }
     TC_CUDA_TRY(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
     const char* at = "qcon";
-    cudaError_t le = cudaSuccess;
-    if (xsplit_) {
-      // A^+ (k_xa) needs only the tile Grams of the previous Y-step: a branch of
-      // the graph that runs beside the Q contraction
-      le = cudaEventRecord(ev_fork_, cap_stream_);
-      if (le == cudaSuccess) le = cudaStreamWaitEvent(aux_stream_, ev_fork_, 0);
-      if (le == cudaSuccess) {
-        at = "xa";
-        xa_fn_<<<S_, kXaThreads, xa_smem_, aux_stream_>>>(d_);
-        le = cudaPeekAtLastError();
-      }
-      if (le == cudaSuccess) le = cudaEventRecord(ev_join_, aux_stream_);
-    }
-    if (le == cudaSuccess) {
-      at = "qcon";
-      launch_qcon(cap_stream_);
-      le = cudaPeekAtLastError();
-    }
-    if (le == cudaSuccess && xsplit_) le = cudaStreamWaitEvent(cap_stream_, ev_join_, 0);
+    launch_qcon(cap_stream_);
+    cudaError_t le = cudaPeekAtLastError();
     if (le == cudaSuccess) {
       at = "xstep";
-      launch_xstep(cap_stream_, xsplit_);
+      launch_xstep(cap_stream_);
       le = cudaPeekAtLastError();
     }
+    bool forked = false;
     if (le == cudaSuccess) {
       at = "ystep";
-      launch_ystep(cap_stream_);
+      // with the four-kernel X-step, A^+ of the next iteration (k_xa) needs only
+      // the tile Grams the Y-step writes: a branch of the graph beside the rest
+      // of the iteration (Z~ synthesis, slab kernel)
+      forked = launch_ystep(cap_stream_, xsplit_ ? aux_stream_ : nullptr);
       le = cudaPeekAtLastError();
     }
     if (le == cudaSuccess) {
@@ -631,6 +619,10 @@ class Engine final : public EngineBase {
       at = "check";
       k_check<T><<<1, 32, 0, cap_stream_>>>(d_);
       le = cudaPeekAtLastError();
+    }
+    if (forked) {
+      const cudaError_t je = cudaStreamWaitEvent(cap_stream_, ev_join_, 0);
+      if (le == cudaSuccess) le = je;
     }
     cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(cap_stream_, out);
@@ -662,7 +654,7 @@ class Engine final : public EngineBase {
       cudaEventRecord(ev[1], stream_);
       launch_xstep(stream_);
       cudaEventRecord(ev[2], stream_);
-      launch_ystep(stream_);
+      launch_ystep(stream_);  // with A^+ of the next X-step (four-kernel form)
       cudaEventRecord(ev[3], stream_);
       launch_slab(MODE_ITER, nullptr, 0, stream_);
       cudaEventRecord(ev[4], stream_);
@@ -703,10 +695,10 @@ class Engine final : public EngineBase {
     slab_[mode]<<<n1_, slab_threads_, slab_smem_, s>>>(d_, Wout, slabs_in_smem_ ? 1 : 0, init);
   }
   void launch_qcon(cudaStream_t s) { qcon_<<<qgrid_, qthreads_, qcon_smem_, s>>>(d_, Q_); }
-  // skip_xa: k_xa was launched on a branch of its own (graph capture)
-  void launch_xstep(cudaStream_t s, bool skip_xa = false) {
+  // With the four-kernel X-step, A^+ (k_xa) is formed after every change of Y~
+  // (initialisation, Y-step), so the X-step starts with it in place.
+  void launch_xstep(cudaStream_t s) {
     if (xsplit_) {
-      if (!skip_xa) xa_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
       if (xb_slice_) xb_<<<S_, 1024, xb_smem_, s>>>(d_, Q_);
       else xb_<<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
       k_xg<T><<<dim3(S_, gch_), 256, xg_smem_, s>>>(d_);
@@ -715,12 +707,27 @@ class Engine final : public EngineBase {
     }
     xstep_<<<S_, xstep_threads(rp_), xstep_smem_, s>>>(d_, Q_, xarrays_in_smem_ ? 1 : 0);
   }
-  void launch_ystep(cudaStream_t s) {
+  // Y-step, then (four-kernel X-step) A^+ of the next X-step from the new tile
+  // Grams.  With a branch stream (graph capture) A^+ is formed there, beside
+  // the rest of the iteration; the return value says whether it was, and the
+  // caller then joins on ev_join_.  Without one it follows on s.
+  bool launch_ystep(cudaStream_t s, cudaStream_t branch = nullptr) {
     const int tw = 32 * ystep_cpl(rp_);
     dim3 g(S_, (n2_ + tw - 1) / tw);
     if (tcy_) tck_.dcon<<<dim3(S_, (n2_ + 127) / 128, ksplit_), 256, tck_.dsm, s>>>(d_);
     ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
+    bool forked = false;
+    if (xsplit_) {
+      if (branch && cudaEventRecord(ev_fork_, s) == cudaSuccess &&
+          cudaStreamWaitEvent(branch, ev_fork_, 0) == cudaSuccess) {
+        xa_fn_<<<S_, kXaThreads, xa_smem_, branch>>>(d_);
+        forked = cudaEventRecord(ev_join_, branch) == cudaSuccess;
+      } else {
+        xa_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
+      }
+    }
     if (tcy_) tck_.zsyn<<<dim3(S_, (n1_ + 127) / 128, (n2_ + 63) / 64), 256, tck_.zsm, s>>>(d_);
+    return forked;
   }
 
   // One TCTF2R iteration: Q = R~Y~^H, X-step (+ Y-step r x r work), Y-step,
