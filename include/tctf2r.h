@@ -110,7 +110,8 @@ typedef struct tc_ctx tc_ctx;
  *            device, 0 if they are host pointers
  *   cuda_stream : cudaStream_t to order all work on (NULL = legacy default)
  * Device memory of the context is allocated here (cudaMalloc) and released by
- * tc_free.  Synchronises the stream before returning.
+ * tc_free; the CUDA graph of one iteration is captured and uploaded here too,
+ * so tc_iterate only launches it.  Synchronises the stream before returning.
  * Errors: TC_ERR_ARG for invalid sizes/parameters/NULL inputs, TC_ERR_NOMEM,
  * TC_ERR_CUDA, TC_ERR_UNSUPPORTED for precisions or options not built. */
 tc_status tc_init(tc_ctx** out, const tc_params* p, const void* G, const uint8_t* mask,

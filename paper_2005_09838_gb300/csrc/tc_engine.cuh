@@ -445,7 +445,14 @@ class Engine final : public EngineBase {
       poisoned_ = true;
       return TC_ERR_CUDA;
     }
-    return check_dev_err(err);
+    tc_status st = check_dev_err(err);
+    if (st != TC_OK) return st;
+    // the iteration graph is built and uploaded here, so that tc_iterate only
+    // launches it
+    st = capture(err);
+    if (st != TC_OK) return st;
+    TC_CUDA_TRY(cudaGraphUpload(graph_exec_, stream_));
+    return TC_OK;
   }
 
   tc_status iterate(int n, int* done, std::string& err) override {
