@@ -68,6 +68,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_workloads(rank):
+    """The bench instances of one rank: one per observed ratio, seeds distinct
+    per rank (each rank completes its own tensors; no data is exchanged)."""
+    out = []
+    for q in OBSERVED:
+        w = wl.c2(q)
+        out.append(wl.Workload(w.name, w.n1, w.n2, w.n3, w.r, w.period, w.observed, w.iters,
+                               w.seed + 7919 * rank))
+    return out
+
+
+def job_throughput(local_ms, units_per_rank, ws, device):
+    """Whole-job rate: the slowest rank's time (all-reduce MAX over ranks when
+    ws > 1) and the units all ranks processed over it.  Returns (ms, units/s)."""
+    total_ms = float(local_ms)
+    if ws > 1:
+        import torch
+        tt = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return total_ms, units_per_rank * ws / (total_ms / 1e3)
+
+
 def workload_config(iters):
     w = wl.c2(0.2)
     return {"workload": "144x288x168 traffic tensor (OD x 5-min slots x days), tubal rank 8, FP32",
@@ -216,9 +239,7 @@ def run_ours(args):
     sptr = stream.cuda_stream
     # resident inputs: one instance per observed ratio (distinct seeds per rank)
     insts, dev_in = [], []
-    for q in OBSERVED:
-        w = wl.c2(q)
-        w = wl.Workload(w.name, w.n1, w.n2, w.n3, w.r, w.period, w.observed, w.iters, w.seed + 7919 * rank)
+    for w in rank_workloads(rank):
         inst = wl.as_precision(wl.generate(w), np.float32)
         insts.append((w, inst))
         dev_in.append((torch.from_numpy(wl.to_colmajor(inst["G"], np.float32)).to(dev),
@@ -262,13 +283,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     t_wall = time.perf_counter() - t_wall0
-    total_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    iters_total = args.iters * args.steps * ws
-    value = iters_total / (total_ms / 1e3)
+    total_ms, value = job_throughput(sum(step_ms), args.iters * args.steps, ws, dev)
 
     # ---- per-kernel device times (CUDA events inside the library), averaged over one
     # completion (100 iterations) of a fresh context ------------------------------------
