@@ -232,13 +232,18 @@ tc_status tc_grad_free(tc_grad* g);
  *   f0      : host pointer receiving f0 of the final iterate, or NULL
  *   cuda_stream : stream to run on; the call synchronises it before returning
  * The first call on a device looks up the device address of the static array
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).  The call reads its results back into host
+ * variables and synchronises the stream, so it must not be made on a stream
+ * that is being captured into a CUDA graph: it then returns TC_ERR_STATE.
  * All calls share the array and it keeps the last call's contents; the call
  * clears what must start at zero.  Calls that overlap on the GPU (other host
  * threads or streams) race on the array and must be serialised by the caller.
- * Errors: TC_ERR_ARG for bad arguments or a problem whose arrays exceed the
- * 16 MiB scratch (the message gives the bytes needed), TC_ERR_UNSUPPORTED,
- * TC_ERR_CUDA, TC_ERR_NUMERIC. */
+ * Errors: TC_ERR_ARG for bad arguments, for a buffer that is not device
+ * memory of the current device (checked with cudaPointerGetAttributes; the
+ * sizes of the buffers cannot be checked and must match the layouts above),
+ * or for a problem whose arrays exceed the 16 MiB scratch (the message gives
+ * the bytes needed), TC_ERR_STATE, TC_ERR_UNSUPPORTED, TC_ERR_CUDA,
+ * TC_ERR_NUMERIC. */
 tc_status tc_complete_static(const tc_params* p, const void* G, const uint8_t* mask, const void* Y0,
                              const void* X0, int32_t n_iters, void* W, double* f0, void* cuda_stream);
 

@@ -120,7 +120,8 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   tc_status s0 = scratch_address(dev, &base);
   if (s0 != TC_OK) return s0;
   int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return sfail(TC_ERR_CUDA, "cudaDeviceGetAttribute (shared memory opt-in limit) failed");
   optin -= kStaticSmemReserve;  // room for the kernels' static shared memory
 
   const int n1 = (int)p.n1, n2 = (int)p.n2, n3 = (int)p.n3, r = p.r, S = n3 / 2 + 1, mw = (n2 + 31) / 32;
@@ -188,23 +189,41 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   slab_table<T, 0>(slab);
   YFn<T> ystep = pick_ystep<T>(rp, !yxg);
   QFn<T> qcon = pick_qcon<T>(rp);
-  for (int m = 0; m < 3; ++m) allow_dynamic_smem((const void*)slab[m], lay.total);
   XFn<T> xstep = pick_xstep_for<T>(rp, false);
-  allow_dynamic_smem((const void*)xstep, xl.total);
-  allow_dynamic_smem((const void*)ystep, ysm);
-  allow_dynamic_smem((const void*)qcon, qsm);
+  const struct {
+    const void* fn;
+    size_t bytes;
+    const char* name;
+  } opt_in[] = {{(const void*)slab[MODE_ITER], lay.total, "slab (iteration)"},
+                {(const void*)slab[MODE_W], lay.total, "slab (W read-back)"},
+                {(const void*)slab[MODE_R], lay.total, "slab (objective)"},
+                {(const void*)xstep, xl.total, "X-step"},
+                {(const void*)ystep, ysm, "Y-step"},
+                {(const void*)qcon, qsm, "Q contraction"}};
+  for (const auto& o : opt_in) {
+    const cudaError_t e = allow_dynamic_smem(o.fn, o.bytes);
+    if (e != cudaSuccess)
+      return sfail(TC_ERR_CUDA, std::string("dynamic shared memory opt-in of ") + std::to_string(o.bytes) +
+                                    " bytes for the " + o.name + " kernel failed: " + cudaGetErrorString(e));
+  }
   const int sis = slabs_in_smem ? 1 : 0;
   const int fgrid = 4 * 152;
 
   // the array keeps the previous call's contents: clear what must start at zero
-  cudaMemsetAsync(d.err, 0, sizeof(int), st);
+  {
+    const cudaError_t e = cudaMemsetAsync(d.err, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+      return sfail(TC_ERR_CUDA, std::string("clearing the device error flag failed: ") + cudaGetErrorString(e));
+  }
   k_static_tables<T><<<3, 256, 0, st>>>(winv, hinv, twg, n1, n2, n3, p.mu, p.rho1, p.rho2);
   k_pack<T><<<n1 * n3, 256, 0, st>>>(static_cast<const T*>(G), mask, Gint, maskbits, n1, n2, n3, mw);
   k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(Y0), d.Yt, n2, r, n3, 1, twg);
   if (X0) {
     k_factor_dft<T><<<fgrid, 256, 0, st>>>(static_cast<const T*>(X0), d.Xt, n1, r, n3, 0, twg);
   } else {
-    cudaMemsetAsync(d.Xt, 0, nx * sizeof(cx<T>), st);
+    const cudaError_t e = cudaMemsetAsync(d.Xt, 0, nx * sizeof(cx<T>), st);
+    if (e != cudaSuccess)
+      return sfail(TC_ERR_CUDA, std::string("clearing X~0 failed: ") + cudaGetErrorString(e));
   }
   k_synth_init<T><<<fgrid, 256, 0, st>>>(d);
   k_gram_tiles<T><<<dim3(S, d.ytiles), 256, 0, st>>>(d);
@@ -254,8 +273,36 @@ extern "C" tc_status tc_complete_static(const tc_params* p, const void* G, const
   if (p->flags != 0 || p->step != TC_STEP_EXACT || p->eps != 0.0)
     return sfail(TC_ERR_UNSUPPORTED, "tc_complete_static runs exact steps for a fixed number of iterations only");
   if (!std::isfinite(p->pinv_rtol) || p->pinv_rtol >= 1.0) return sfail(TC_ERR_ARG, "pinv_rtol must be < 1");
+  if (p->precision != TC_FP64 && p->precision != TC_FP32) return sfail(TC_ERR_UNSUPPORTED, "precision not built");
   const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the call reads results back to host variables and synchronises the
+    // stream, neither of which a stream capture allows
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess)
+      return sfail(TC_ERR_CUDA, "cudaStreamIsCapturing failed on the given stream");
+    if (cs != cudaStreamCaptureStatusNone)
+      return sfail(TC_ERR_STATE, "tc_complete_static must not be called on a stream that is being captured");
+  }
+  // every buffer must be device memory of the current device (a host pointer
+  // would be dereferenced by the kernels)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return sfail(TC_ERR_CUDA, "cudaGetDevice failed");
+  const struct {
+    const void* ptr;
+    const char* name;
+  } bufs[] = {{G, "G"}, {mask, "mask"}, {Y0, "Y0"}, {X0, "X0"}, {W, "W"}};
+  for (const auto& b : bufs) {
+    if (!b.ptr) continue;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, b.ptr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return sfail(TC_ERR_ARG, std::string(b.name) + " is not a pointer the CUDA runtime knows");
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev)
+      return sfail(TC_ERR_ARG, std::string(b.name) + " must be device memory of the current device");
+  }
   if (p->precision == TC_FP64) return run_static<double>(*p, G, mask, Y0, X0, n_iters, W, f0, st);
-  if (p->precision == TC_FP32) return run_static<float>(*p, G, mask, Y0, X0, n_iters, W, f0, st);
-  return sfail(TC_ERR_UNSUPPORTED, "precision not built");
+  return run_static<float>(*p, G, mask, Y0, X0, n_iters, W, f0, st);
 }

@@ -280,12 +280,40 @@ class GradContext:
         self.close()
 
 
+def _check_static_buffers(params: tc_params, G, mask, Y0, X0, W):
+    """The buffers of tc_complete_static must be contiguous CUDA tensors on the
+    current device with the element type and element count the parameters
+    imply; anything else is refused here, before the kernels could read or
+    write outside a buffer."""
+    import torch
+    real = torch.float64 if params.precision == TC_FP64 else torch.float32
+    n1, n2, n3, r = params.n1, params.n2, params.n3, params.r
+    want = {"G": (G, real, n1 * n2 * n3), "mask": (mask, torch.uint8, n1 * n2 * n3),
+            "Y0": (Y0, real, r * n2 * n3), "W": (W, real, n1 * n2 * n3)}
+    if X0 is not None:
+        want["X0"] = (X0, real, n1 * r * n3)
+    dev = torch.cuda.current_device()
+    for name, (t, dtype, numel) in want.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor (tc_complete_static takes device buffers only)")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype} for this precision, got {t.dtype}")
+        if t.numel() != numel:
+            raise ValueError(f"{name} must hold {numel} elements, got {t.numel()}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+
+
 def complete_static(params: tc_params, G, mask, Y0, n_iters: int, W, X0=None, stream: int | None = None,
                     want_f0: bool = True):
     """tc_complete_static: the whole completion with no device allocation, for
     callers that cannot call cudaMalloc (their device memory belongs to a host
     framework's allocator, or a cudaMalloc would stall a latency-critical
-    loop).  All buffers are device tensors; returns f0 (or None)."""
+    loop).  All buffers are CUDA tensors on the current device, checked for
+    element type and count before the call; returns f0 (or None)."""
+    _check_static_buffers(params, G, mask, Y0, X0, W)
     lib = load()
     f0 = ctypes.c_double()
     st = lib.tc_complete_static(ctypes.byref(params), _ptr(G), _ptr(mask), _ptr(Y0), _ptr(X0), int(n_iters), _ptr(W),
