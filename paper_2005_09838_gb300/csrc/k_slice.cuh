@@ -167,6 +167,21 @@ __device__ __forceinline__ df df_rcp(df a) {
   return df_add(df{y0, 0.0f}, df_mul(df{y0, 0.0f}, e));
 }
 
+// s + c += a b with the rounding errors of the product (FMA) and of the sum
+// (Knuth's two-sum) collected in c: about twice the working precision.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ void dot2(T& s, T& c, T a, T b) {
+  const T p = mul_rn(a, b);  // not contracted: the FMA below recovers its rounding error
+  const T pe = fma(a, b, -p);
+  const T t = s + p;
+  const T z = t - s;
+  c += ((s - (t - z)) + (p - z)) + pe;
+  s = t;
+}
+
 // gauss_jordan_inplace on an FP64 matrix, with the arithmetic in df64 (the
 // matrix is converted, eliminated and converted back; no FP64 instruction in
 // the elimination itself).
@@ -792,8 +807,9 @@ __host__ __device__ inline XLayout xstep_layout(int n1, int n2, int r, bool arra
   XLayout L{};
   const size_t rr = (size_t)r * r;
   size_t off = 0;
-  L.mats = off;  // A, A^+, P, V, work (2), G, Dg, pivots, reductions
-  off = align_up(off + (rr * 8 + 3 * (size_t)r + 2) * sizeof(cx<TS>), 16);
+  L.mats = off;  // A, A^+, P, V, work (2), G, Dg, pivots, reductions (complex doubles:
+                 // the FP64 real-slice solve of an FP32 engine uses the same region)
+  off = align_up(off + (rr * 8 + 3 * (size_t)r + 2) * sizeof(cx<double>), 16);
   L.ht = off;
   off = align_up(off + sizeof(T) * 2 * n1, 16);
   if (arrays_in_smem) {
@@ -897,6 +913,101 @@ __device__ __forceinline__ cx<T> hth_at(const cx<T>* x, int i, int n1) {
 template <typename T, typename S>
 __device__ __forceinline__ cx<T> cvt(cx<S> v) {
   return cx<T>{(T)v.re, (T)v.im};
+}
+
+// ---------------------------------------------------------------------------
+// Y-step Gram of a real slice (k = 0, and k = n3/2 for even n3) in an FP32
+// engine, in FP64 accuracy.  X~' of a real slice is real, and for traffic data
+// the DC slice is badly conditioned: it carries the mean traffic, the columns
+// of X~'_0 lie close together, and G = X~'^H H_rho1 X~' reaches a condition
+// number near 2e6 along a completion of the 144 x 288 x 168 tensor at 40-60%
+// observed, while every other slice stays below 1e2.  An FP32 G^+ has entries
+// of size 1/lambda_min; their rounding reaches the new Y~ amplified by that
+// condition number.  So on these slices G and Dg are accumulated with
+// error-free products and sums (the callers), the pseudo-inverse is taken in
+// df64 arithmetic with the FP64 path's cutoff (d.rtol64), and t G^+ is kept in
+// FP64 (d.Gp64, slot 0 for k = 0, slot 1 for the Nyquist slice) so that
+// k_ystep applies it in FP64.
+//
+// M: 7 r^2 + 3 r + 2 complex doubles of shared memory holding G (first r^2,
+// row-major) and Dg (at 6 r^2, after the 2 r^2 work area) on entry.  Every thread of the block calls it.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr size_t real_gram_doubles(int r) { return 7 * (size_t)r * r + 3 * (size_t)r + 2; }
+// Where the callers leave G and Dg in M (the layout below).
+__device__ __forceinline__ cx<double>* real_gram_G(cx<double>* M, int) { return M; }
+__device__ __forceinline__ cx<double>* real_gram_Dg(cx<double>* M, int rr) { return M + 6 * rr; }
+
+template <typename T, int RP>
+__device__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
+  const int r = d.r, rr = r * r, tid = threadIdx.x, nt = blockDim.x;
+  cx<double>* G64 = real_gram_G(M, rr);
+  cx<double>* Ap64 = G64 + rr;
+  cx<double>* P64 = Ap64 + rr;
+  cx<double>* V64 = P64 + rr;
+  cx<double>* W64 = V64 + rr;  // 2 r^2
+  cx<double>* Dg64 = real_gram_Dg(M, rr);
+  cx<double>* piv64 = Dg64 + rr;  // 3 r
+  double* sred = reinterpret_cast<double*>(piv64 + 3 * r);  // 4
+  const double rtol = d.rtol64;
+  if (d.scaled) {
+    // lambda_max of G for the step beta / L2 (the eigendecomposition in FP32;
+    // the inverse below is the df64 one whenever it is certified)
+    jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);
+    __syncthreads();
+  }
+  block_pinv_herm<double, RP, true>(G64, Ap64, P64, V64, W64, piv64, sred, r, rtol, false);
+  const double t2 = d.scaled ? ((sred[2] > 0.0) ? (double)d.beta / sred[2] : 0.0) : 1.0;
+  const int slot = (k == 0) ? 0 : 1;
+  for (int e = tid; e < rr; e += nt) {
+    const double g = Ap64[e].re * t2;
+    d.Gp64[(size_t)slot * rr + e] = cx<double>{g, 0.0};
+    d.Gp[(size_t)k * rr + e] = cx<T>{(T)g, T(0)};
+    d.Dg[(size_t)k * rr + e] = cx<T>{(T)Dg64[e].re, T(0)};
+  }
+}
+
+// G = X~'^H H_rho1 X~' and Dg = -(X~'^H (X~' - X~) + rho1 (H X~')^H (H X~')) of
+// a real slice from the real parts of X~' (Xn) and X~ (Xo), [r][n1] each, with
+// dot2 accumulation; tp adjacent threads per entry split the rows and their
+// (sum + compensation) values are added in FP64.  Writes G and Dg in the
+// layout of real_gram_solve_store.
+template <typename T>
+__device__ void real_gram_accumulate(const Dev<T>& d, const cx<T>* Xn, const cx<T>* Xo, cx<double>* M) {
+  const int n1 = d.n1, r = d.r, rr = r * r, tid = threadIdx.x, nt = blockDim.x;
+  const double rho1 = (double)d.rho1;
+  int tp = 1;
+  while (tp < 32 && tp * 2 * rr <= nt) tp *= 2;
+  const int q = tid & (tp - 1);
+  for (int base = 0; base < rr * tp; base += nt) {  // every thread runs the same passes
+    const int task = (base + tid) / tp;
+    double a0 = 0.0, hh = 0.0, dd = 0.0;
+    if (task < rr) {
+      const int s = task / r, u = task - s * r;
+      const cx<T>* xs = Xn + (size_t)s * n1;
+      const cx<T>* xu = Xn + (size_t)u * n1;
+      const cx<T>* ou = Xo + (size_t)u * n1;
+      T s0 = T(0), c0 = T(0), s1 = T(0), c1 = T(0), s2 = T(0), c2 = T(0);
+      for (int i = q; i < n1; i += tp) {
+        const T a = xs[i].re, b = xu[i].re;
+        dot2(s0, c0, a, b);
+        dot2(s2, c2, a, b - ou[i].re);
+        if (i + 1 < n1) dot2(s1, c1, a - xs[i + 1].re, b - xu[i + 1].re);
+      }
+      a0 = (double)s0 + (double)c0;
+      hh = (double)s1 + (double)c1;
+      dd = (double)s2 + (double)c2;
+    }
+    for (int o = tp >> 1; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      hh += __shfl_xor_sync(0xffffffffu, hh, o);
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    }
+    if (task < rr && q == 0) {
+      real_gram_G(M, rr)[task] = cx<double>{a0 + rho1 * hh, 0.0};
+      real_gram_Dg(M, rr)[task] = cx<double>{-(dd + rho1 * hh), 0.0};
+    }
+  }
+  __syncthreads();
 }
 
 // TS is the type of the two r x r pseudo-inverses (double in the precision
@@ -1033,6 +1144,14 @@ __global__ void __launch_bounds__(xstep_threads(RP), 1) k_xstep(Dev<T> d, const 
   if (d.conv) block_max_to(dmax, d.conv + 0);
   __syncthreads();
 
+  if (sizeof(T) == 4 && realslice) {
+    // FP64-accurate Gram, df64 pseudo-inverse, FP64 G^+ (see real_gram_solve_store)
+    cx<double>* M64 = reinterpret_cast<cx<double>*>(smem + lay.mats);
+    real_gram_accumulate<T>(d, Ts, Xs, M64);
+    real_gram_solve_store<T, RP>(d, k, M64);
+    for (int e = tid; e < r * n1; e += blockDim.x) Xg[e] = Ts[e];
+    return;
+  }
   // ---- G = X~'^H H_rho1 X~' (Hermitian) and Dg = E - G ----------------------------------
   // (H X~')^H (H X~') = sum_i conj(x_i - x_{i+1}) (x_i - x_{i+1}) row by row.
   // tp adjacent threads share one (s, u) pair and split the rows; their partial
@@ -1150,6 +1269,16 @@ constexpr int kYThreads = 256;
 
 __host__ __device__ constexpr int ystep_cpl(int rp) { return rp <= 16 ? 2 : 1; }
 
+// Shared memory of k_ystep: partial sums, D, old and new Y~ of the tile, Dg,
+// G^+, X~' of the slice (XSH), then r^2 doubles for the FP64 G^+ of a real slice.
+template <typename T>
+__host__ __device__ inline size_t ystep_gh64_offset(int n1, int r, int rp, bool x_in_smem, bool tcy) {
+  const size_t tw = 32 * (size_t)ystep_cpl(rp);
+  return align_up(((size_t)((tcy ? 0 : kYThreads / 32) + 3) * rp * tw + 2 * (size_t)r * r +
+                   (x_in_smem && !tcy ? (size_t)r * n1 : 0)) *
+                      sizeof(cx<T>),
+                  16);
+}
 // TCY (precision form, r > 16): D comes as ksplit partial sums over ranges of
 // n1 from k_dcon_tc (d.Dpart) and Z~ is formed by k_zsyn_tc afterwards.
 // XSH: X~' of the slice staged in shared memory (the compiler then sees
@@ -1174,9 +1303,14 @@ __device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem)
     for (int e = tid; e < r * n1; e += blockDim.x) xs[e] = Xg[e];
     Xs = xs;
   }
+  // real slices of an FP32 engine: t G^+ in FP64 (k_xstep / k_xc), applied in FP64
+  const bool realslice = (k == 0) || (2 * k == d.n3);
+  const bool g64 = sizeof(T) == 4 && realslice && d.Gp64 != nullptr;
+  double* gh64 = reinterpret_cast<double*>(smem + ystep_gh64_offset<T>(n1, r, RP, XSH, TCY));
   for (int e = tid; e < rr; e += blockDim.x) {
     Dgs[e] = d.Dg[(size_t)k * rr + e];
     Gh[e] = d.Gp[(size_t)k * rr + e];
+    if (g64) gh64[e] = d.Gp64[(size_t)(k == 0 ? 0 : 1) * rr + e].re;
   }
   for (int e = tid; e < r * TW; e += blockDim.x) {
     const int s = e / TW, c = e - s * TW;
@@ -1258,7 +1392,6 @@ __device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem)
     Ds[s * TW + c] = v;
   }
   __syncthreads();
-  const bool realslice = (k == 0) || (2 * k == d.n3);
   double dmax = 0.0;
   for (int e = tid; e < RP * TW; e += blockDim.x) {
     const int s = e / TW, c = e - s * TW;
@@ -1267,7 +1400,13 @@ __device__ __forceinline__ void ystep_impl(const Dev<T>& d, unsigned char* smem)
       continue;
     }
     cx<T> y = Yo[e];
-    for (int u = 0; u < r; ++u) cfma(y, Gh[s * r + u], Ds[u * TW + c]);
+    if (g64) {
+      double yd = (double)y.re;
+      for (int u = 0; u < r; ++u) yd = fma(gh64[s * r + u], (double)Ds[u * TW + c].re, yd);
+      y.re = (T)yd;
+    } else {
+      for (int u = 0; u < r; ++u) cfma(y, Gh[s * r + u], Ds[u * TW + c]);
+    }
     if (realslice) y.im = T(0);
     d.Yt[((size_t)k * r + s) * n2 + j0 + c] = y;
     Yn[e] = y;
@@ -1336,10 +1475,7 @@ __global__ void __launch_bounds__(kYThreads) k_ystep(Dev<T> d) {
 
 template <typename T>
 __host__ inline size_t ystep_smem_bytes(int n1, int r, int rp, bool x_in_smem = true, bool tcy = false) {
-  const size_t tw = 32 * (size_t)ystep_cpl(rp);
-  return ((size_t)((tcy ? 0 : kYThreads / 32) + 3) * rp * tw + 2 * (size_t)r * r +
-          (x_in_smem && !tcy ? (size_t)r * n1 : 0)) *
-         sizeof(cx<T>);
+  return ystep_gh64_offset<T>(n1, r, rp, x_in_smem, tcy) + (size_t)r * r * sizeof(double);
 }
 
 template <typename T>

@@ -240,21 +240,6 @@ __global__ void __launch_bounds__(1024, 1) k_xb1(Dev<T> d, const cx<T>* __restri
   if (d.conv) block_max_to(dmax, d.conv + 0);
 }
 
-// s + c += a b with the rounding errors of the product (FMA) and of the sum
-// (Knuth's two-sum) collected in c: about twice the working precision.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-
-template <typename T>
-__device__ __forceinline__ void dot2(T& s, T& c, T a, T b) {
-  const T p = mul_rn(a, b);  // not contracted: the FMA below recovers its rounding error
-  const T pe = fma(a, b, -p);
-  const T t = s + p;
-  const T z = t - s;
-  c += ((s - (t - z)) + (p - z)) + pe;
-  s = t;
-}
-
 // ---- partial Grams over kXgRows rows -----------------------------------------------------
 // The real slices (DC and, for even n3, Nyquist) hold real factors; their
 // Grams are the ill-conditioned ones (the DC slice carries the mean traffic),
@@ -417,6 +402,24 @@ __global__ void __launch_bounds__(kXaThreads) k_xc(Dev<T> d) {
   const bool realslice = (k == 0) || (2 * k == d.n3);
   const double rho1 = (double)d.rho1;
   const cx<T>* part = d.Gpart + (size_t)k * d.gch * 3 * rr;
+  const cx<T>* Xp = d.Tb + (size_t)k * r * n1;
+  cx<T>* X = d.Xt + (size_t)k * r * n1;
+  const int nx = r * n1, nt = blockDim.x;
+  if (sizeof(T) == 4 && realslice) {
+    // FP64 G^+ of a real slice (real_gram_solve_store); the partials are the
+    // compensated sums of k_xg
+    cx<double>* M64 = reinterpret_cast<cx<double>*>(smem);
+    for (int task = tid; task < rr; task += blockDim.x) {
+      cx<double> a0, hh, dd;
+      sum_partials(part, rr, d.gch, task, true, a0, hh, dd);
+      real_gram_G(M64, rr)[task] = cx<double>{a0.re + rho1 * hh.re, 0.0};
+      real_gram_Dg(M64, rr)[task] = cx<double>{-(dd.re + rho1 * hh.re), 0.0};
+    }
+    __syncthreads();
+    real_gram_solve_store<T, 32>(d, k, M64);
+    for (int e = tid; e < nx; e += nt) X[e] = Xp[e];
+    return;
+  }
   for (int task = tid; task < rr; task += blockDim.x) {
     const int s = task / r, u = task - s * r;
     cx<double> a0, hh, dd;
@@ -441,9 +444,6 @@ __global__ void __launch_bounds__(kXaThreads) k_xc(Dev<T> d) {
     d.Dg[(size_t)k * rr + e] = cvt<T>(Dgm[e]);
     d.Gp[(size_t)k * rr + e] = gp;
   }
-  const cx<T>* Xp = d.Tb + (size_t)k * r * n1;
-  cx<T>* X = d.Xt + (size_t)k * r * n1;
-  const int nx = r * n1, nt = blockDim.x;
   int e = tid;
   for (; e + 3 * nt < nx; e += 4 * nt) {  // four loads in flight per thread
     cx<T> v[4];

@@ -208,6 +208,8 @@ class Engine final : public EngineBase {
     cx<T>* Yt = alloc<cx<T>>(ny, err);
     cx<T>* Dg = alloc<cx<T>>(nrr, err);
     cx<T>* Gp = alloc<cx<T>>(nrr, err);
+    // FP64 t G^+ of the real slices (DC, Nyquist) of an FP32 engine
+    cx<double>* Gp64 = sizeof(T) == 4 ? alloc<cx<double>>((size_t)2 * r_ * r_, err) : nullptr;
     T* winv = alloc<T>((size_t)6 * n2_, err);
     T* hinv = alloc<T>((size_t)2 * n1_, err);
     cx<T>* twg = alloc<cx<T>>((size_t)n3_, err);
@@ -270,7 +272,8 @@ class Engine final : public EngineBase {
     // r x r work is small and the extra launches and barriers dominate: 35 us
     // against 49 us for the 144 x 288 x 168, r = 8 workload)
     const bool s64 = solve64<T>(rp_, mixed_);
-    const size_t xa_bytes = s64 ? xa_smem_bytes<double>(r_) : xa_smem_bytes<T>(r_);
+    // FP32 engines: room for the FP64 real-slice solve of k_xc (real_gram_solve_store)
+    const size_t xa_bytes = (s64 || sizeof(T) == 4) ? xa_smem_bytes<double>(r_) : xa_smem_bytes<T>(r_);
     xsplit_ = (sizeof(T) == 4 ? rp_ >= 16 : rp_ == 32) && xb_smem_bytes<T>(n1_) <= (size_t)optin &&
               xa_bytes <= (size_t)optin && xg_smem_bytes<T>(r_) <= (size_t)optin;
     if (xsplit_) {
@@ -388,6 +391,8 @@ class Engine final : public EngineBase {
     d_.part_k = part_k;
     d_.err = derr;
     d_.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : default_rtol<T>(r_, rp_, mixed_);
+    d_.rtol64 = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r_ * std::numeric_limits<double>::epsilon();
+    d_.Gp64 = Gp64;
     d_.scaled = (p.step == TC_STEP_SCALED) ? 1 : 0;
     d_.alpha = (T)p.alpha;
     d_.beta = (T)p.beta;

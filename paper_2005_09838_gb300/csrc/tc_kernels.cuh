@@ -38,6 +38,8 @@ struct Dev {
   int ytiles;       // ceil(n2 / 32)
   cx<T>* Dg;        // [S][r][r] E - G of the Y-step (k_xstep)
   cx<T>* Gp;        // [S][r][r] G^+
+  cx<double>* Gp64; // [2][r][r] t G^+ of the real slices (DC, Nyquist) in FP64; FP32 engines only
+  double rtol64;    // pseudo-inverse cutoff of the FP64-accurate real-slice solves
   cx<T>* Tb;        // [S][3][r][n1] X-step work arrays when shared memory is too small
   const T* winv;    // [6][n2] W-step run tables (wstep_tables)
   const T* hinv;    // [2][n1] H_rho1 = I + rho1 H^T H: inverse pivots and rho1 * inverse pivots

@@ -155,6 +155,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   d.Yt = cv.take<cx<T>>(ny);
   d.Dg = cv.take<cx<T>>(nrr);
   d.Gp = cv.take<cx<T>>(nrr);
+  d.Gp64 = sizeof(T) == 4 ? cv.take<cx<double>>((size_t)2 * r * r) : nullptr;
   T* winv = cv.take<T>((size_t)6 * n2);
   T* hinv = cv.take<T>((size_t)2 * n1);
   cx<T>* twg = cv.take<cx<T>>((size_t)n3);
@@ -183,6 +184,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   d.twg = twg;
   d.yx_global = yxg ? 1 : 0;
   d.rtol = (p.pinv_rtol > 0) ? p.pinv_rtol : default_rtol<T>(r, rp, false);
+  d.rtol64 = (p.pinv_rtol > 0) ? p.pinv_rtol : (double)r * std::numeric_limits<double>::epsilon();
 
   // ---- kernels (generic mode-3 transform) ------------------------------------------------
   SlabFn<T> slab[3];
