@@ -100,6 +100,27 @@ def test_degenerate_masks_fp64():
     assert _rel(got["W"], ref["W"]) <= TOL["fp64"]
 
 
+@pytest.mark.parametrize("n3", [112, 168])
+def test_degenerate_masks_fp32_shared_memory_transform(n3):
+    # the same run boundaries through the FP32 slab kernel with the
+    # shared-memory transform and the table-driven W-step: fully observed and
+    # fully missing OD rows, a missing frontal slice, j = 0 always missing and
+    # j = n2 - 1 always observed, ragged n2 (two mask words), r = 1
+    w = wl.custom(8, 37, n3, 1, 0.5, seed=5 + n3, iters=10)
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    mask = inst["mask"].copy()
+    mask[0, :, :] = True
+    mask[1, :, :] = False
+    mask[:, :, 3] = False
+    mask[:, 0, :] = False
+    mask[:, -1, :] = True
+    inst["mask"] = mask
+    inst["G"] = np.where(mask, inst["M"], 0.0)
+    _, ref, got = _run_pair(w, "R", "fp32", w.iters, inst=inst)
+    assert _rel(got["W"], ref["W"]) <= TOL["fp32"]
+    assert abs(got["f0"] - ref["f0"]) <= TOL["fp32"] * abs(ref["f0"])
+
+
 def test_fully_observed_exact_rank_recovery_fp64():
     # Proposition "tubrank": exact low-tubal-rank data, fully observed
     rng = np.random.default_rng(3)
@@ -200,13 +221,12 @@ def test_rank32_long_slices(precision):
 
 def test_c3_full_size_three_iterations_fp32():
     # the precision-form workload (529 x 96 x 112, r = 32, 30% observed) in
-    # plain FP32, first three iterations against the oracle.  Bound 5e-5, not
-    # 1e-5: the Gram X~'^H H_rho1 X~' of the DC slice has condition number
-    # 1.5e4 - 3.6e4 over these iterations, and the FP32 rounding of X~' and of
-    # the contractions that feed it (relative 2^-24 per value) reaches the
-    # solve with that amplification even though the solve itself is carried
-    # in FP64 storage; measured 1.3e-5 - 2.1e-5 on W and f0.
+    # plain FP32, first three iterations against the oracle.  The Gram
+    # X~'^H H_rho1 X~' of the DC slice has condition number 1.5e4 - 3.6e4 over
+    # these iterations: its FP64 pseudo-inverse is applied in FP64 (real-slice
+    # path of the FP32 engine)
     w = wl.c3(0.3)
     inst, ref, got = _run_pair(w, "R", "fp32", 3)
-    assert _rel(got["W"], ref["W"]) <= 5e-5
-    assert abs(got["f0"] - ref["f0"]) <= 5e-5 * abs(ref["f0"])
+    print(f"C3 FP32: W {_rel(got['W'], ref['W']):.2e}, f0 {abs(got['f0'] - ref['f0']) / abs(ref['f0']):.2e}")
+    assert _rel(got["W"], ref["W"]) <= TOL["fp32"]
+    assert abs(got["f0"] - ref["f0"]) <= TOL["fp32"] * abs(ref["f0"])

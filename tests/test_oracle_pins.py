@@ -294,6 +294,56 @@ def test_scaled_steps_are_descent_directions():
     assert h(Xn, Yn) < h(Xn, Y)
 
 
+def _path_laplacian_norm(m):
+    # H^T H for the first-difference matrix of Eq. (Toeplitz) is the Laplacian
+    # of the path on m nodes, with eigenvalues 2 - 2 cos(pi k / m), k = 0..m-1
+    return 2.0 + 2.0 * math.cos(math.pi / m)
+
+
+def test_scaled_x_step_length_is_alpha_over_closed_form_L1():
+    # Eq. (updataXYW1): the scaled X-step is X + (alpha / L1) d_X with
+    # L1 = ||H_rho1||_2 ||Y Y^*||_2.  Rows of Y~ with disjoint supports make the
+    # Gram diagonal, diag(d_s^2), so ||Y Y^*||_2 = max d_s^2 (not a Frobenius
+    # norm), and ||H_rho1||_2 = 1 + rho1 (2 + 2 cos(pi / m1)).  The scaled step
+    # divided by the unit step is alpha / L1.
+    rng = _rng(41)
+    m1, m2, r = 7, 11, 3
+    d = np.array([0.7, 2.5, 1.3])
+    Y = np.zeros((r, m2), complex)
+    for s in range(r):
+        Y[s, 2 * s + 1] = d[s] * np.exp(1j * rng.uniform(0, 2 * np.pi))
+    X = rng.standard_normal((m1, r)) + 1j * rng.standard_normal((m1, r))
+    W = rng.standard_normal((m1, m2)) + 1j * rng.standard_normal((m1, m2))
+    rho1, alpha = 0.4, 0.9
+    L1 = (1.0 + rho1 * _path_laplacian_norm(m1)) * d.max() ** 2
+    step_unit = O.x_update(X, Y, W, rho1) - X
+    step_scaled = O.x_update(X, Y, W, rho1, step="scaled", alpha=alpha) - X
+    np.testing.assert_allclose(step_scaled, (alpha / L1) * step_unit, rtol=1e-12, atol=0)
+
+
+def test_scaled_y_step_length_is_beta_over_closed_form_L2():
+    # L2 = ||X^* H_rho1 X||_2.  The DCT-II vectors v_k(i) = cos(pi k (i + 1/2) / m1)
+    # are the eigenvectors of the path Laplacian H^T H (eigenvalues
+    # 2 - 2 cos(pi k / m1)); with the columns of X~ equal to c_k v_k / ||v_k|| (and a
+    # phase each), X^* H_rho1 X = diag(c_k^2 (1 + rho1 (2 - 2 cos(pi k / m1)))).
+    rng = _rng(42)
+    m1, m2 = 9, 10
+    ks, c = [1, 4, 8], [1.5, 0.8, 1.1]
+    i = np.arange(m1)
+    cols = []
+    for k, ck in zip(ks, c):
+        v = np.cos(math.pi * k * (i + 0.5) / m1)
+        cols.append(ck * np.exp(1j * rng.uniform(0, 2 * np.pi)) * v / np.linalg.norm(v))
+    X = np.stack(cols, axis=1)
+    Y = rng.standard_normal((3, m2)) + 1j * rng.standard_normal((3, m2))
+    W = rng.standard_normal((m1, m2)) + 1j * rng.standard_normal((m1, m2))
+    rho1, beta = 0.7, 0.6
+    L2 = max(ck ** 2 * (1.0 + rho1 * (2.0 - 2.0 * math.cos(math.pi * k / m1))) for k, ck in zip(ks, c))
+    step_unit = O.y_update(X, Y, W, rho1) - Y
+    step_scaled = O.y_update(X, Y, W, rho1, step="scaled", beta=beta) - Y
+    np.testing.assert_allclose(step_scaled, (beta / L2) * step_unit, rtol=1e-12, atol=0)
+
+
 # --------------------------------------------------------------------------
 # The TCTF2R Algorithm: invariants and special cases
 # --------------------------------------------------------------------------
