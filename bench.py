@@ -221,6 +221,42 @@ def ncu_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+def iteration_bytes(w, s=4):
+    """Algorithmic bytes of one iteration: the observed tensor (s N), the mask
+    (N bits) and three passes over the half spectrum of the residual (read by
+    the X-step contraction, read by the Y-step contraction, written by the
+    fused transform / W-step / residual step)."""
+    return s * w.N + w.N / 8 + 3 * (2 * s * w.n1 * w.n2 * w.S)
+
+
+def algorithmic_bytes(w, s=4):
+    """Algorithmic bytes per launch of each kernel of the iteration, by the
+    steps it carries: Q = R~Y~^H one read of R~ (plus the factors), the X-step
+    the factors and the tile Grams, the Y-step one read of R~ (plus the
+    factors), the slab kernel G, the mask bits and one write of R~.  Their sum
+    is iteration_bytes plus the factor traffic."""
+    n1, n2, r, S = w.n1, w.n2, w.r, w.S
+    rt = 2 * s * n1 * n2 * S
+    fx, fy = 2 * s * r * n1 * S, 2 * s * r * n2 * S
+    ag = 16 * S * ((n2 + 31) // 32) * (r * (r + 1) // 2)
+    return {"qcon": rt + fy + fx, "xstep": 3 * fx + ag, "ystep": rt + fx + 2 * fy + ag,
+            "slab": s * w.N + w.N / 8 + rt}
+
+
+def design_bytes(w, s=4):
+    """Bytes each kernel of this design moves, including the spectrum Z~ that
+    the Y-step writes and the slab kernel reads back (a design choice: the
+    synthesis Z~ = X~Y~ could run inside the slab kernel instead) and the mask
+    as 32-bit row words."""
+    n1, n2, r, S = w.n1, w.n2, w.r, w.S
+    rt = 2 * s * n1 * n2 * S
+    fx, fy = 2 * s * r * n1 * S, 2 * s * r * n2 * S
+    ag = 16 * S * ((n2 + 31) // 32) * (r * (r + 1) // 2)
+    maskb = 4 * n1 * w.n3 * ((n2 + 31) // 32)
+    return {"qcon": rt + fy + fx, "xstep": 3 * fx + ag, "ystep": 2 * rt + fx + 2 * fy + ag,
+            "slab": s * w.N + maskb + 2 * rt}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -294,16 +330,7 @@ def run_ours(args):
     pc.close()
     ctxs = []
     names = ("qcon", "xstep", "ystep", "slab")
-    s = 4
-    n1, n2, r = w0.n1, w0.n2, w0.r
-    rt = 2 * s * n1 * n2 * S           # one pass over a half spectrum of the slab (R~ or Z~)
-    fx, fy = 2 * s * r * n1 * S, 2 * s * r * n2 * S
-    ag = 16 * S * ((n2 + 31) // 32) * (r * (r + 1) // 2)   # FP64 tile Grams of Y~
-    maskb = 4 * n1 * n2 * ((w0.n3 + 31) // 32)              # mask words
-    alg = {"qcon": rt + fy + fx,                 # R~, Y~ in; Q out
-           "xstep": 3 * fx + ag,                 # X~, Q in; X~' out; tile Grams in
-           "ystep": 2 * rt + fx + 2 * fy + ag,   # R~, X~', Y~ in; Y~', Z~, tile Grams out
-           "slab": s * N + maskb + 2 * rt}       # G, mask, Z~ in; R~ out
+    alg, design = algorithmic_bytes(w0), design_bytes(w0)
     dom = names[int(np.argmax(prof))]
     peaks = {}
     try:
@@ -314,11 +341,17 @@ def run_ours(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = alg[dom] / (prof[names.index(dom)] * 1e-3) / 1e9
     traffic = ncu_traffic() if dom == "slab" else None
+    b_iter = iteration_bytes(w0)
+    it_ms = total_ms / (args.iters * args.steps)  # device time per iteration of the timed region
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg[dom],
+                "design_bytes_per_launch": design[dom],
                 "kernel_ms": {n: v for n, v in zip(names, prof)},
-                "iteration_alg_bytes": sum(alg.values()),
+                "iteration_alg_bytes": b_iter,
+                "iteration_ms": it_ms,
+                "iteration_frac": b_iter / (it_ms * 1e-3) / 1e9 / peak,
+                "iteration_design_bytes": sum(design.values()),
                 "iteration_ms_sum_of_kernels": sum(prof)}
 
     # ---- recovery accuracy: FP32 vs the FP64 GPU path, 100 iterations, 20% mask ---------

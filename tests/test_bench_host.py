@@ -10,6 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 import bench  # noqa: E402
+import workloads as wl  # noqa: E402
 
 
 def test_batched_workload_is_seeded_and_in_range():
@@ -34,3 +35,17 @@ def test_source_hash_covers_the_slab_kernel_sources():
     csrc = os.path.join(ROOT, "paper_2005_09838_gb300", "csrc")
     for f in bench.SLAB_SOURCES:
         assert os.path.exists(os.path.join(csrc, f)), f
+
+
+def test_roofline_bytes_follow_the_per_iteration_model():
+    # the bench's algorithmic bytes for the 144 x 288 x 168 FP32 workload:
+    # B_iter = s N + N/8 + 3 (2 s n1 n2 S) = 113.3 MB per iteration, of which
+    # the fused transform / W-step / residual kernel carries G, the mask bits
+    # and one write of the residual spectrum (56.94 MB)
+    import bench
+    w = wl.c2(0.2)
+    assert abs(bench.iteration_bytes(w) - 113.3e6) < 0.05e6
+    alg = bench.algorithmic_bytes(w)
+    assert abs(alg["slab"] - 56.94e6) < 0.01e6
+    # the slab kernel's design bytes add the read of the stored Z~ spectrum
+    assert bench.design_bytes(w)["slab"] - alg["slab"] > 28e6
