@@ -26,7 +26,7 @@ namespace tc {
 // call it.  Returns (block-uniform) 1 if the inverse path was taken.
 // ---------------------------------------------------------------------------
 template <typename TS, bool DF>
-__device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
+__device__ __noinline__ void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
                                        int r, TS rtol, TS* lmax_out);
 
 // Frobenius norm of the r x r block at column col0 of a row-major matrix with
@@ -294,7 +294,7 @@ __device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in)
 
 // DF: the block inverse (r > 16) of an FP64 matrix runs in df64 arithmetic.
 template <typename T, int RP, bool DF = false>
-__device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
+__device__ __noinline__ int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
                                       int r, T rtol, bool force_eig = false) {
   const int tid = threadIdx.x, nt = blockDim.x;
   int ok;
@@ -371,7 +371,7 @@ __device__ inline int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>
 // |a_pq| <= 4 u max(|a_pp|, |a_qq|) (u the unit roundoff), and the sweeps stop
 // after one without rotations.
 template <typename T>
-__device__ inline void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+__device__ __noinline__ void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
                                          T rtol, T* lmax_out) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
@@ -481,7 +481,7 @@ __device__ inline void block_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx
 // barriers of block_jacobi_pinv would cost more than the rotations: then A^+
 // and P = A A^+ with the cutoff rule.
 template <typename T>
-__device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
+__device__ __noinline__ void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, int r,
                                         T rtol, T* lmax_out) {
   const int lane = threadIdx.x & 31;
   const T u_round = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-8f);
@@ -598,7 +598,7 @@ __device__ inline void warp_jacobi_pinv(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<
 // r 2^-23 lambda_max: the Gram was accumulated in FP32 and cannot resolve
 // smaller eigenvalues.
 template <typename TS, bool DF>
-__device__ inline void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
+__device__ __noinline__ void jacobi_fallback(const cx<TS>* A, cx<TS>* Ap, cx<TS>* P, cx<TS>* V, cx<TS>* W, cx<TS>* piv,
                                        int r, TS rtol, TS* lmax_out) {
   const bool small = r <= 16;  // one warp; the other threads wait at the caller's barrier
   if constexpr (DF && sizeof(TS) == 8) {
@@ -937,8 +937,42 @@ __host__ __device__ constexpr size_t real_gram_doubles(int r) { return 7 * (size
 __device__ __forceinline__ cx<double>* real_gram_G(cx<double>* M, int) { return M; }
 __device__ __forceinline__ cx<double>* real_gram_Dg(cx<double>* M, int rr) { return M + 6 * rr; }
 
+// Gauss-Jordan inverse (no pivoting) of a real symmetric positive definite
+// r x r matrix in FP64 by the whole block, one element per thread and pivot;
+// a: r^2 doubles (row-major), work: 2 r^2 doubles (the inverse ends in its
+// first half), piv: 2 doubles.  Returns 0 (block-uniform) when a pivot is not
+// positive.  The FP64 pipe is slow on this part, but an 8 x 8 or 16 x 16
+// elimination is a few hundred operations per pivot.
+static __device__ __noinline__ int real_gj_fp64(const double* a, double* work, double* piv, int r) {
+  const int t = threadIdx.x, nt = blockDim.x, rr = r * r;
+  for (int e = t; e < rr; e += nt) work[e] = a[e];
+  if (t == 0) piv[0] = (a[0] > 0.0 && isfinite(a[0])) ? 1.0 / a[0] : 0.0;
+  __syncthreads();
+  for (int p = 0; p < r; ++p) {
+    const double* src = work + (p & 1) * rr;
+    double* dst = work + ((p + 1) & 1) * rr;
+    const double ip = piv[p & 1];
+    if (!(ip > 0.0)) return 0;
+    for (int e = t; e < rr; e += nt) {
+      const int i = e / r, j = e - i * r;
+      double v;
+      if (i == p) v = (j == p) ? ip : src[p * r + j] * ip;
+      else if (j == p) v = -src[i * r + p] * ip;
+      else v = fma(-src[i * r + p], src[p * r + j] * ip, src[e]);
+      dst[e] = v;
+      if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = (v > 0.0 && isfinite(v)) ? 1.0 / v : 0.0;
+    }
+    __syncthreads();
+  }
+  if (r & 1) {
+    for (int e = t; e < rr; e += nt) work[e] = work[rr + e];
+    __syncthreads();
+  }
+  return 1;
+}
+
 template <typename T, int RP>
-__device__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
+__device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
   const int r = d.r, rr = r * r, tid = threadIdx.x, nt = blockDim.x;
   cx<double>* G64 = real_gram_G(M, rr);
   cx<double>* Ap64 = G64 + rr;
@@ -955,7 +989,36 @@ __device__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
     jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);
     __syncthreads();
   }
-  block_pinv_herm<double, RP, true>(G64, Ap64, P64, V64, W64, piv64, sred, r, rtol, false);
+  // FP64 Gauss-Jordan on the real Gram, accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
+  // (then lambda_min > rtol lambda_max: nothing is cut, G^+ = G^-1); otherwise the
+  // eigendecomposition fallback applies the cutoff
+  double* g = reinterpret_cast<double*>(Ap64);      // r^2 real values of G
+  double* wk = reinterpret_cast<double*>(W64);      // 2 r^2
+  double* pv = reinterpret_cast<double*>(piv64);    // 2
+  for (int e = tid; e < rr; e += nt) g[e] = G64[e].re;
+  __syncthreads();
+  int ok = real_gj_fp64(g, wk, pv, r);
+  if (tid < 32) {
+    double an = 0.0, in = 0.0;
+    for (int e = tid; e < rr; e += 32) {
+      an += g[e] * g[e];
+      in += wk[e] * wk[e];
+    }
+    an = warp_sum(an);
+    in = warp_sum(in);
+    if (tid == 0) sred[1] = (ok && isfinite(in) && sqrt(an) * sqrt(in) < 0.5 / rtol) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (sred[1] != 0.0) {
+    for (int e = tid; e < rr; e += nt) {
+      const int i = e / r, j = e - i * r;
+      const double v = 0.5 * (wk[i * r + j] + wk[j * r + i]);
+      Ap64[e] = cx<double>{v, 0.0};  // g (aliasing Ap64) is no longer read
+    }
+  } else {
+    jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);
+  }
+  __syncthreads();
   const double t2 = d.scaled ? ((sred[2] > 0.0) ? (double)d.beta / sred[2] : 0.0) : 1.0;
   const int slot = (k == 0) ? 0 : 1;
   for (int e = tid; e < rr; e += nt) {
@@ -972,7 +1035,7 @@ __device__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
 // (sum + compensation) values are added in FP64.  Writes G and Dg in the
 // layout of real_gram_solve_store.
 template <typename T>
-__device__ void real_gram_accumulate(const Dev<T>& d, const cx<T>* Xn, const cx<T>* Xo, cx<double>* M) {
+__device__ __noinline__ void real_gram_accumulate(const Dev<T>& d, const cx<T>* Xn, const cx<T>* Xo, cx<double>* M) {
   const int n1 = d.n1, r = d.r, rr = r * r, tid = threadIdx.x, nt = blockDim.x;
   const double rho1 = (double)d.rho1;
   int tp = 1;
@@ -1041,24 +1104,41 @@ __global__ void __launch_bounds__(xstep_threads(RP), 1) k_xstep(Dev<T> d, const 
   cx<T>* Ts;
   cx<T>* Xg = d.Xt + (size_t)k * r * n1;
   const cx<T>* Qg = Qin + (size_t)k * r * n1;
+  // the slice's X~, Q and the H_rho1 pivots go to shared memory by asynchronous
+  // copies, all in flight while A is summed below
   if (arrays_in_smem) {
     Xs = reinterpret_cast<cx<T>*>(smem + lay.xs);
     Qs = reinterpret_cast<cx<T>*>(smem + lay.qs);
     Ts = reinterpret_cast<cx<T>*>(smem + lay.ts);
     for (int e = tid; e < r * n1; e += blockDim.x) {
-      Xs[e] = Xg[e];
-      Qs[e] = Qg[e];
+      cp_async_elem(Xs + e, Xg + e);
+      cp_async_elem(Qs + e, Qg + e);
     }
   } else {
     Xs = Xg;
     Qs = const_cast<cx<T>*>(Qg);
     Ts = d.Tb + (size_t)k * r * n1;
   }
-  for (int i = tid; i < 2 * n1; i += blockDim.x) hinv[i] = d.hinv[i];
+  for (int i = tid; i < 2 * n1; i += blockDim.x) cp_async_elem(hinv + i, d.hinv + i);
   const bool realslice = (k == 0) || (2 * k == d.n3);
   const T rho1 = d.rho1;
   const TS rtol = (TS)d.rtol;
 
+  constexpr bool kDF = sizeof(T) == 4 && sizeof(TS) == 8;  // FP64 solves of an FP32 engine: df64
+  bool certA;
+  T t1;
+  if (d.apre) {
+    // A^+, P, the certificate and the step along d_X were formed by k_xa from the
+    // tile Grams of the last Y-step
+    for (int e = tid; e < rr; e += blockDim.x) {
+      Ap[e] = cvt<TS>(d.Apg[(size_t)k * rr + e]);
+      P[e] = cvt<TS>(d.Pg[(size_t)k * rr + e]);
+    }
+    certA = d.certA[k] != 0;
+    t1 = d.tstep[k];
+    cp_async_wait_all();
+    __syncthreads();
+  } else {
   // ---- A = Y~Y~^H: FP64 sums of the 32-column tile Grams written by k_ystep ----------
   {
     const int ntask = r * (r + 1) / 2;
@@ -1079,11 +1159,12 @@ __global__ void __launch_bounds__(xstep_threads(RP), 1) k_xstep(Dev<T> d, const 
       A[u * r + s] = cx<TS>{(TS)v.re, (TS)(-v.im)};
     }
   }
+  cp_async_wait_all();
   __syncthreads();
-  constexpr bool kDF = sizeof(T) == 4 && sizeof(TS) == 8;  // FP64 solves of an FP32 engine: df64
-  const bool certA = block_pinv_herm<TS, RP, kDF>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0) != 0;
+  certA = block_pinv_herm<TS, RP, kDF>(A, Ap, P, V, Wk, pivbuf, sred, r, rtol, d.scaled != 0) != 0;
   // step along d_X: 1, or alpha / L1 with L1 = ||H_rho1||_2 lambda_max(A)
-  const T t1 = d.scaled ? ((sred[2] > TS(0)) ? d.alpha / (d.hnorm * (T)sred[2]) : T(0)) : T(1);
+  t1 = d.scaled ? ((sred[2] > TS(0)) ? d.alpha / (d.hnorm * (T)sred[2]) : T(0)) : T(1);
+  }
 
   // ---- B = Q A^+ - rho1 (H^T H X~) P ------------------------------------------------------
   // A^+ and P in T (the work area of the solve is free again); a thread forms

@@ -276,6 +276,22 @@ class Engine final : public EngineBase {
     const size_t xa_bytes = (s64 || sizeof(T) == 4) ? xa_smem_bytes<double>(r_) : xa_smem_bytes<T>(r_);
     xsplit_ = (sizeof(T) == 4 ? rp_ >= 16 : rp_ == 32) && xb_smem_bytes<T>(n1_) <= (size_t)optin &&
               xa_bytes <= (size_t)optin && xg_smem_bytes<T>(r_) <= (size_t)optin;
+    // one-CTA X-step: A^+ of the next X-step formed by k_xa on a graph branch after
+    // each Y-step (beside Z~ synthesis and the slab kernel), off the critical path
+    apre_ = !xsplit_ && xa_bytes <= (size_t)optin;
+    d_.apre = apre_ ? 1 : 0;
+    if (apre_) {
+      xa_threads_ = 64;
+      while (xa_threads_ < r_ * r_ && xa_threads_ < kXaThreads) xa_threads_ *= 2;
+      d_.Apg = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
+      d_.Pg = alloc<cx<T>>((size_t)S_ * r_ * r_, err);
+      d_.certA = alloc<int>((size_t)S_, err);
+      d_.tstep = alloc<T>((size_t)S_, err);
+      if (!err.empty()) return TC_ERR_NOMEM;
+      xa_smem_ = xa_bytes;
+      xa_fn_ = s64 ? k_xa<T, double> : k_xa<T, T>;
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)xa_fn_, xa_smem_));
+    }
     if (xsplit_) {
       gch_ = (n1_ + kXgRows - 1) / kXgRows;
       d_.gch = gch_;
@@ -286,6 +302,7 @@ class Engine final : public EngineBase {
       d_.Gpart = alloc<cx<T>>((size_t)S_ * gch_ * 3 * r_ * r_, err);
       if (!err.empty()) return TC_ERR_NOMEM;
       xa_smem_ = xa_bytes;
+      xa_threads_ = kXaThreads;
       xa_fn_ = s64 ? k_xa<T, double> : k_xa<T, T>;
       xc_fn_ = s64 ? k_xc<T, double> : k_xc<T, T>;
       // one CTA per slice when its Q fits in shared memory, else a CTA per 8 columns
@@ -440,7 +457,7 @@ class Engine final : public EngineBase {
     }
     k_synth_init<T><<<fgrid, 256, 0, stream_>>>(d_);                    // Z~0 = X~0 Y~0
     k_gram_tiles<T><<<dim3(S_, ytiles), 256, 0, stream_>>>(d_);         // A of the first X-step
-    if (xsplit_) xa_fn_<<<S_, kXaThreads, xa_smem_, stream_>>>(d_);     // its A^+
+    if (xsplit_ || apre_) xa_fn_<<<S_, xa_threads_, xa_smem_, stream_>>>(d_);  // its A^+
     launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - Z0)
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(stream_);
@@ -599,7 +616,7 @@ class Engine final : public EngineBase {
       err = std::string("pending error before graph capture: ") + cudaGetErrorString(pre);
       return TC_ERR_CUDA;
     }
-    if (xsplit_ && !aux_stream_) {
+    if ((xsplit_ || apre_) && !aux_stream_) {
       TC_CUDA_TRY(cudaStreamCreateWithFlags(&aux_stream_, cudaStreamNonBlocking));
       TC_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
       TC_CUDA_TRY(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
@@ -619,7 +636,7 @@ class Engine final : public EngineBase {
       // with the four-kernel X-step, A^+ of the next iteration (k_xa) needs only
       // the tile Grams the Y-step writes: a branch of the graph beside the rest
       // of the iteration (Z~ synthesis, slab kernel)
-      forked = launch_ystep(cap_stream_, xsplit_ ? aux_stream_ : nullptr);
+      forked = launch_ystep(cap_stream_, (xsplit_ || apre_) ? aux_stream_ : nullptr);
       le = cudaPeekAtLastError();
     }
     if (le == cudaSuccess) {
@@ -729,13 +746,13 @@ class Engine final : public EngineBase {
     if (tcy_) tck_.dcon<<<dim3(S_, (n2_ + 127) / 128, ksplit_), 256, tck_.dsm, s>>>(d_);
     ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
     bool forked = false;
-    if (xsplit_) {
+    if (xsplit_ || apre_) {
       if (branch && cudaEventRecord(ev_fork_, s) == cudaSuccess &&
           cudaStreamWaitEvent(branch, ev_fork_, 0) == cudaSuccess) {
-        xa_fn_<<<S_, kXaThreads, xa_smem_, branch>>>(d_);
+        xa_fn_<<<S_, xa_threads_, xa_smem_, branch>>>(d_);
         forked = cudaEventRecord(ev_join_, branch) == cudaSuccess;
       } else {
-        xa_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
+        xa_fn_<<<S_, xa_threads_, xa_smem_, s>>>(d_);
       }
     }
     if (tcy_) tck_.zsyn<<<dim3(S_, (n1_ + 127) / 128, (n2_ + 63) / 64), 256, tck_.zsm, s>>>(d_);
@@ -796,6 +813,8 @@ class Engine final : public EngineBase {
   bool xarrays_in_smem_ = true;
   bool mixed_ = false;
   bool xsplit_ = false;  // X-step as four kernels
+  bool apre_ = false;    // one-CTA X-step with A^+ from k_xa on a graph branch
+  int xa_threads_ = kXaThreads;
   YFn<T> xa_fn_ = nullptr, xc_fn_ = nullptr;
   int gch_ = 0;
   size_t xa_smem_ = 0, xb_smem_ = 0, xg_smem_ = 0;

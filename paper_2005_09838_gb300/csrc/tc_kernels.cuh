@@ -69,6 +69,8 @@ struct Dev {
   T* tstep;          // [S] step t1 along d_X
   cx<T>* Gpart;      // [S][gch][3][r][r] partial Grams over kXgRows rows
   int gch;
+  int apre;          // 1: A^+, P, certA, tstep of the one-CTA X-step come from k_xa (run on a
+                     // graph branch after each Y-step) instead of being formed in k_xstep
 };
 
 // True once the stopping test has fired: the iteration kernels return at once.
