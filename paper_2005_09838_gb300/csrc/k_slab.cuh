@@ -198,6 +198,95 @@ __device__ void wstep_sweeps(T* __restrict__ col, int LP, const uint32_t* __rest
     wstep_bwd_word<T, true, false>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
 }
 
+// ---------------------------------------------------------------------------
+// The same W-step with each row split into nseg segments of whole mask words,
+// one thread per (row, segment): a block-wide call that takes three barriers.
+// Both recurrences restart at every observed entry (there a_j = 0 and c_j = 0:
+// the value is G), and the backward one also at j = n2 - 1.  So the value
+// entering a segment follows from the entries between the last restart and
+// the segment boundary, and each thread recomputes it with the very operations
+// the sequential sweep would apply (results are bit-identical to
+// wstep_sweeps): forward, from the last observed entry before the segment (or
+// j = 0); backward, from the first observed entry at or after the segment's
+// end (or j = n2 - 1).  The carries are formed before the values they read
+// are overwritten.
+//   item: this thread's (row, segment) index, row = item % nrows, segment =
+//         item / nrows; items >= nrows * nseg only join the barriers
+//   col(l): the row's first entry; rows are strided by LP along j
+// ---------------------------------------------------------------------------
+template <typename T, typename ColFn>
+__device__ void wstep_sweeps_seg(ColFn col_of, int LP, const uint32_t* __restrict__ msk, int* __restrict__ stw,
+                                 int nrows, int nseg, int item, int n2, T rho2, const T* __restrict__ wtab) {
+  const int words = (n2 + 31) >> 5;
+  const int ql = n2 - 32 * (words - 1);  // entries in the last word
+  const int wps = (words + nseg - 1) / nseg;
+  const bool active = item < nrows * nseg;
+  const int l = active ? item % nrows : 0, sg = active ? item / nrows : 0;
+  const int w0 = min(sg * wps, words), w1 = min(w0 + wps, words);
+  const bool work = active && w0 < w1;
+  T* col = col_of(l);
+  const uint32_t* rowm = msk + (size_t)l * ((n2 + 31) >> 5);
+  int* rowst = stw + (size_t)l * ((n2 + 31) >> 5);
+  auto bit = [&](int j) { return (rowm[j >> 5] >> (j & 31)) & 1u; };
+
+  // ---- forward carry: d_{j0 - 1} and the run start entering word w0 -------------------
+  T d = T(0);
+  int st = 0;
+  if (work && w0 > 0) {
+    for (int w = w0 - 1; w >= 0; --w) {
+      const uint32_t mw = rowm[w];
+      if (mw) {
+        st = 32 * w + 32 - __clz(mw);
+        break;
+      }
+    }
+    const int j0 = 32 * w0;
+    if (st > 0) d = col[(size_t)(st - 1) * LP];  // observed: the recurrence restarts at G
+    for (int j = st; j < j0; ++j) {             // the run of missing entries up to the boundary
+      const T inv = wtab[((st == 0) ? 0 : n2) + (j - st)];
+      d = fma(rho2 * inv, d, col[(size_t)j * LP] * inv);
+    }
+  }
+  __syncthreads();
+  // ---- forward sweep of the segment -----------------------------------------------------
+  if (work) {
+    for (int w = w0; w < w1; ++w) {
+      const uint32_t mw = rowm[w];
+      rowst[w] = st;
+      if (w < words - 1) wstep_fwd_word<T, true, false>(col, LP, mw, w, 32, st, n2, rho2, wtab, d);
+      else if (ql == 32) wstep_fwd_word<T, true, true>(col, LP, mw, w, 32, st, n2, rho2, wtab, d);
+      else wstep_fwd_word<T, false, true>(col, LP, mw, w, ql, st, n2, rho2, wtab, d);
+      if (mw) st = 32 * w + 32 - __clz(mw);
+    }
+  }
+  __syncthreads();
+  // ---- backward carry: w_{j1}, j1 = 32 w1, from the first restart at or after it --------
+  T wn = T(0);
+  if (work && w1 < words) {
+    const int j1 = 32 * w1;
+    int k = j1;
+    while (k < n2 - 1 && !bit(k)) ++k;
+    wn = col[(size_t)k * LP];  // w_k = d_k at a restart
+    for (int j = k - 1; j >= j1; --j) {
+      const int w = j >> 5, q = j & 31;
+      const uint32_t below = rowm[w] & ((1u << q) - 1u);
+      const int rs = below ? 32 * w + 32 - __clz(below) : rowst[w];
+      const T c = wtab[2 * n2 + ((rs == 0) ? 0 : n2) + (j - rs)];
+      wn = fma(c, wn, col[(size_t)j * LP]);
+    }
+  }
+  __syncthreads();
+  // ---- backward sweep of the segment ----------------------------------------------------
+  if (work) {
+    for (int w = w1 - 1; w >= w0; --w) {
+      if (w < words - 1) wstep_bwd_word<T, true, false>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
+      else if (ql == 32) wstep_bwd_word<T, true, true>(col, LP, rowm[w], w, 32, rowst[w], n2, wtab, wn);
+      else wstep_bwd_word<T, false, true>(col, LP, rowm[w], w, ql, rowst[w], n2, wtab, wn);
+    }
+  }
+  __syncthreads();
+}
+
 // Weighted |W~^{l+1} - W~^l|^2 of one half-spectrum entry: W~ = Z~ + R~, so the
 // change is (R~new - R~old) + (Z~new - Z~old); weight 1 for the real slices
 // (k = 0 and, for even n3, k = n3/2), 2 for the others (their mirror).

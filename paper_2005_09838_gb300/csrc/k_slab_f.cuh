@@ -282,9 +282,10 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
 
   // ---- W-step (one thread per row) ---------------------------------------------------------
   if (wsolve) {
-    for (int l = tid; l < L; l += nt)
-      wstep_sweeps<T>(buf + slab_f_off<N1, N2>(l), LP, msk + l * mw, stw + l * mw, n2, d.rho2, wtab);
-    __syncthreads();
+    // rows split into nseg segments so that every thread has one (row, segment)
+    const int nseg = max(1, nt / L);
+    auto col_of = [&](int l) { return buf + slab_f_off<N1, N2>(l); };
+    wstep_sweeps_seg<T>(col_of, LP, msk, stw, L, nseg, tid, n2, d.rho2, wtab);
   }
 
   // ---- C1: forward DFT_N2 over slots N2 k1 + j, twiddle w_M^{k1 q} -----------------------
