@@ -11,8 +11,11 @@ L2 is flushed (512 MiB write) before every timed step.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on the same workload instead (bounded samples on the host cores).
+On one GPU the default line also carries, under ``forms``, shorter
+measurements of the precision form, the batched form and the differentiation
+form (529 x 288 x 168, r = 16, block gradient descent); ``--no-forms`` skips them.
 
-Two more forms, each one JSON line of its own (not the default):
+The first two forms also have JSON lines of their own:
 ``--form precision``: the 529 x 96 x 112 tensor (529 OD pairs x 96
 fifteen-minute slots x 112 days), tubal rank 32, 30% observed; the precision
 form (TF32 / BF16 tensor-core contractions, FP64-storage solves) against the
@@ -58,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-nmse", action="store_true")
     ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision / batched / differentiation "
+                    "measurements nested in the default line")
     return ap.parse_args()
 
 
@@ -407,6 +412,23 @@ def run_ours(args):
                "sample": f"{n_it} TCTF2R iterations of the 144x288x168 instance (20% observed), {t:.1f} s"}
 
     clocks = clk.summary()
+    # ---- the precision, batched and differentiation forms (one GPU only) -----------------
+    forms = None
+    if not args.no_forms and rank == 0 and ws == 1:
+        forms = {}
+        small = max(2, min(args.steps, 3))
+        try:
+            forms["precision"] = precision_form(torch, dev, stream, flush, small, 2, names=("fp32", "tf32", "bf16"))
+        except Exception as exc:  # reported, not hidden: the headline line still prints
+            forms["precision"] = {"error": repr(exc)}
+        try:
+            forms["batched"] = batched_form(torch, dev, stream, flush, small, 1)
+        except Exception as exc:
+            forms["batched"] = {"error": repr(exc)}
+        try:
+            forms["differentiation"] = grad_form(torch, dev, small)
+        except Exception as exc:
+            forms["differentiation"] = {"error": repr(exc)}
     if rank == 0:
         cfg = workload_config(args.iters)
         cfg["parallelism"] = f"replicas x{ws} (independent completions per GPU)"
@@ -416,7 +438,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 4 * args.iters * args.steps, "clocks": clocks, "nmse": nmse}
+                "gpu_launches": 5 * args.iters * args.steps, "clocks": clocks, "nmse": nmse, "forms": forms}
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
@@ -452,53 +474,112 @@ def _timed(torch, stream, flush, fn, steps, warmup):
     return sum(ms)
 
 
+def precision_form(torch, dev, stream, flush, steps, warmup, names=None, with_nmse=True):
+    """The precision form on the 529 x 96 x 112 workload (r = 32, 30% observed):
+    completions of 30 iterations per step on resident inputs, per form; recovery
+    NMSE of each against the FP64 path after the same iterations."""
+    from paper_2005_09838_gb300 import tc, api
+    sptr = stream.cuda_stream
+    w = wl.c3(0.3)
+    iters = w.iters
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    forms = {"fp32": (tc.TC_FP32, 0), "tf32": (tc.TC_TF32, 0), "bf16": (tc.TC_BF16, 0),
+             "tf32_single_pass": (tc.TC_TF32, tc.TC_FLAG_SINGLE_PASS),
+             "bf16_single_pass": (tc.TC_BF16, tc.TC_FLAG_SINGLE_PASS)}
+    if names:
+        forms = {k: v for k, v in forms.items() if k in names}
+    rates, kern = {}, {}
+    for name, (prec, fl) in forms.items():
+        # one completion (30 iterations from the initial point) per step, each on a
+        # context initialised before the timed region
+        cs = [_resident(tc, torch, dev, w, inst, prec, fl, sptr) for _ in range(warmup + steps)]
+        it = iter(cs)
+        ms = _timed(torch, stream, flush, lambda: next(it).iterate(iters, count=False), steps, warmup)
+        rates[name] = iters * steps / (ms / 1e3)
+        kern[name] = dict(zip(("qcon", "xstep", "ystep", "slab"), cs[0].profile(10)))
+        for c in cs:
+            c.close()
+    nmse = {}
+    if with_nmse:
+        for name in ["fp64"] + [n for n in ("fp32", "tf32", "bf16") if n in forms]:
+            o = api.complete(inst["G"], inst["mask"], inst["Y0"], w.r, iters, *WEIGHTS.values(), name,
+                             objective=False)
+            nmse[name] = wl.nmse(inst["M"], o["W"], inst["mask"])
+    return {"workload": "529x96x112 traffic tensor (OD x 15-min slots x days), tubal rank 32, 30% observed",
+            "iters_per_step": iters, "iters_per_s": rates,
+            "speedup_vs_fp32": {k: v / rates["fp32"] for k, v in rates.items()} if "fp32" in rates else None,
+            "kernel_ms_after_30_iters": kern, "nmse": nmse,
+            "nmse_abs_diff_vs_fp64": {k: abs(v - nmse["fp64"]) for k, v in nmse.items()} if nmse else None,
+            "entries_per_s": {k: v * w.N for k, v in rates.items()}}
+
+
 def run_precision(args):
     import torch
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     from paper_2005_09838_gb300 import build as _b
     _b.build()
-    from paper_2005_09838_gb300 import tc, api
     stream = torch.cuda.current_stream()
-    sptr = stream.cuda_stream
-    w = wl.c3(0.3)
-    iters = w.iters
-    inst = wl.as_precision(wl.generate(w), np.float32)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    forms = {"fp32": (tc.TC_FP32, 0), "tf32": (tc.TC_TF32, 0), "bf16": (tc.TC_BF16, 0),
-             "tf32_single_pass": (tc.TC_TF32, tc.TC_FLAG_SINGLE_PASS),
-             "bf16_single_pass": (tc.TC_BF16, tc.TC_FLAG_SINGLE_PASS)}
-    rates, kern = {}, {}
     with ClockSampler(0) as clk:
-        for name, (prec, fl) in forms.items():
-            # one completion (the configured 30 iterations from the initial point) per step,
-            # each on a context initialised before the timed region
-            cs = [_resident(tc, torch, dev, w, inst, prec, fl, sptr) for _ in range(args.warmup + args.steps)]
-            it = iter(cs)
-            ms = _timed(torch, stream, flush, lambda: next(it).iterate(iters, count=False), args.steps, args.warmup)
-            rates[name] = iters * args.steps / (ms / 1e3)
-            kern[name] = dict(zip(("qcon", "xstep", "ystep", "slab"), cs[0].profile(10)))
-            for c in cs:
-                c.close()
-    nmse = {}
-    if not args.no_nmse:
-        for name, prec in (("fp64", "fp64"), ("fp32", "fp32"), ("tf32", "tf32"), ("bf16", "bf16")):
-            o = api.complete(inst["G"], inst["mask"], inst["Y0"], w.r, iters, *WEIGHTS.values(), prec, objective=False)
-            nmse[name] = wl.nmse(inst["M"], o["W"], inst["mask"])
-    N = w.N
+        res = precision_form(torch, dev, stream, flush, args.steps, args.warmup, with_nmse=not args.no_nmse)
+    rates = res["iters_per_s"]
+    w = wl.c3(0.3)
     line = {"metric": "completion iters/s, precision form (TF32 tensor-core contractions, FP64-storage solves) "
                       "vs plain FP32, 529x96x112 r=32",
             "value": rates["tf32"], "unit": "iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": iters * 1e3 / rates["tf32"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": w.iters * 1e3 / rates["tf32"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "tf32 (split operands) / f32", "data": "synthetic",
-            "config": {"workload": "529x96x112 traffic tensor (OD x 15-min slots x days), tubal rank 32, 30% observed",
-                       "iters_per_step": iters, "weights": WEIGHTS, "l2": "flushed before every timed step",
-                       "entries_per_s": rates["tf32"] * N},
-            "forms_iters_per_s": rates, "speedup_vs_fp32": {k: v / rates["fp32"] for k, v in rates.items()},
-            "kernel_ms_after_30_iters": kern, "nmse": nmse,
-            "nmse_abs_diff_vs_fp64": {k: abs(v - nmse["fp64"]) for k, v in nmse.items()} if nmse else None,
-            "gpu_launches_per_iter": 6, "clocks": clk.summary()}
+            "config": {"workload": res["workload"], "iters_per_step": w.iters, "weights": WEIGHTS,
+                       "l2": "flushed before every timed step", "entries_per_s": rates["tf32"] * w.N},
+            "forms_iters_per_s": rates, "speedup_vs_fp32": res["speedup_vs_fp32"],
+            "kernel_ms_after_30_iters": res["kernel_ms_after_30_iters"], "nmse": res["nmse"],
+            "nmse_abs_diff_vs_fp64": res["nmse_abs_diff_vs_fp64"], "gpu_launches_per_iter": 6,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+
+
+def grad_form(torch, dev, steps):
+    """The differentiation form on the 529 x 288 x 168 workload (r = 16, 20%
+    observed, rho1 = 1e-3, FP32): device time of one loss-and-gradient
+    evaluation through torch.autograd at the seeded initial factors, and of one
+    block step of block gradient descent (gradient plus backtracking
+    evaluations)."""
+    from paper_2005_09838_gb300 import autograd as ag
+    w = wl.c4(0.2)
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    rng = np.random.default_rng(w.seed + 17)
+    X = torch.tensor(rng.standard_normal((w.n1, w.r, w.n3)), dtype=torch.float32, device=dev)
+    Y = torch.tensor(inst["Y0"], dtype=torch.float32, device=dev)
+    g = ag.grad_context(inst["G"], inst["mask"], w.r, 1e-3, dtype=torch.float32)
+    Xr, Yr = X.clone().requires_grad_(True), Y.clone().requires_grad_(True)
+
+    def evaluate():
+        Xr.grad = None
+        Yr.grad = None
+        ag.factor_loss(Xr, Yr, g).backward()
+
+    for _ in range(2):
+        evaluate()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        evaluate()
+    torch.cuda.synchronize()
+    t_eval = (time.perf_counter() - t0) / steps
+    Xf, Yf = np.fft.fft(X.cpu().numpy(), axis=2), np.fft.fft(inst["Y0"], axis=2)
+    Ly = max(np.linalg.norm(Yf[:, :, k] @ Yf[:, :, k].conj().T, 2) for k in range(w.n3))
+    Lx = max(np.linalg.norm(Xf[:, :, k].conj().T @ Xf[:, :, k], 2) for k in range(w.n3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, hist = ag.block_gradient_descent(g, X, Y, steps, 1.0 / Ly, 1.0 / Lx)
+    torch.cuda.synchronize()
+    t_bgd = (time.perf_counter() - t0) / (2 * steps)
+    g.close()
+    return {"workload": "529x288x168 traffic tensor, tubal rank 16, 20% observed, rho1 = 1e-3, FP32",
+            "ms_per_loss_and_gradient": 1e3 * t_eval, "ms_per_block_step": 1e3 * t_bgd,
+            "loss_first": hist[0], "loss_last": hist[-1], "block_steps": 2 * steps,
+            "entries_per_s_loss_and_gradient": w.N / t_eval}
 
 
 # ---------------------------------------------------------------------------
@@ -519,33 +600,35 @@ def batch_workloads():
     return out
 
 
-def _gen32(w):
+NMSE_SAMPLE = range(0, BATCH, 8)  # instances whose recovery NMSE is compared (every eighth)
+
+
+def _gen32_m(args):
+    w, want_m = args
     inst = wl.as_precision(wl.generate(w), np.float32)
+    m = inst["M"].astype(np.float32) if want_m else None
     return (wl.to_colmajor(inst["G"], np.float32), wl.to_colmajor(inst["mask"], np.uint8),
-            wl.to_colmajor(inst["Y0"], np.float32))
+            wl.to_colmajor(inst["Y0"], np.float32), m, inst["mask"] if want_m else None)
 
 
-def run_batched(args):
+def batched_form(torch, dev, stream, flush, steps, warmup):
+    """The batched form: 64 seeded instances advanced together by one graph
+    launch per iteration (mixed: TF32 tensor-core contractions where r > 16;
+    fp32: plain FP32), against the same contexts iterated one after the other,
+    and the recovery NMSE of every eighth instance (mixed against fp32, after
+    the same iterations)."""
     import multiprocessing as mp
-    ws = batch_workloads()
-    # inputs drawn on the host cores before any CUDA call (spawned workers)
-    with mp.get_context("spawn").Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
-        data = pool.map(_gen32, ws)
-    import torch
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    from paper_2005_09838_gb300 import build as _b
-    _b.build()
     from paper_2005_09838_gb300 import tc
-    stream = torch.cuda.current_stream()
+    ws = batch_workloads()
+    with mp.get_context("spawn").Pool(min(len(os.sched_getaffinity(0)), 32)) as pool:
+        data = pool.map(_gen32_m, [(w, q in NMSE_SAMPLE) for q, w in enumerate(ws)])
     sptr = stream.cuda_stream
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     iters = 10
     entries = sum(w.N for w in ws)
 
     def contexts(mixed):
         cs = []
-        for w, (g, m, y) in zip(ws, data):
+        for w, (g, m, y, _, _) in zip(ws, data):
             prec = tc.TC_TF32 if (mixed and w.r > 16) else tc.TC_FP32
             p = tc.make_params(w.n1, w.n2, w.n3, w.r, WEIGHTS["mu"], WEIGHTS["rho1"], WEIGHTS["rho2"], prec)
             cs.append(tc.Completion(p, torch.from_numpy(g).to(dev), torch.from_numpy(m).to(dev),
@@ -553,32 +636,62 @@ def run_batched(args):
             torch.cuda.synchronize()
         return cs
 
-    res = {}
+    res, nmse = {}, {}
+    for label, mixed in (("mixed", True), ("fp32", False)):
+        cs = contexts(mixed)
+        with tc.Batch(cs, stream=sptr) as B:
+            B.iterate(2 * 4)  # tuning trials (two per candidate branch count), real iterations
+            ms = _timed(torch, stream, flush, lambda: B.iterate(iters), steps, warmup)
+            res[f"batch_{label}"] = BATCH * iters * steps / (ms / 1e3)
+            res[f"branches_{label}"] = B.branches()
+        ms = _timed(torch, stream, flush, lambda: [c.iterate(iters, count=False) for c in cs], steps, warmup)
+        res[f"sequential_{label}"] = BATCH * iters * steps / (ms / 1e3)
+        for q in NMSE_SAMPLE:
+            W, _, _ = cs[q].result_numpy()
+            w = ws[q]
+            Mq, maskq = data[q][3], data[q][4]
+            nmse.setdefault(q, {})[label] = wl.nmse(Mq.astype(np.float64),
+                                                    wl.from_colmajor(W, (w.n1, w.n2, w.n3)).astype(np.float64),
+                                                    maskq)
+        for c in cs:
+            c.close()
+        torch.cuda.synchronize()
+    diffs = [abs(v["mixed"] - v["fp32"]) for v in nmse.values()]
+    return {"workload": "64 traffic tensors, n1 64-1024, n2 96-288, n3 28-168, r 4-32, 10-60% observed",
+            "instances": [w.name for w in ws], "iters_per_step": iters, "entries_total": entries,
+            "instance_iters_per_s": res,
+            "speedup_batched_mixed_vs_sequential_fp32": res["batch_mixed"] / res["sequential_fp32"],
+            "speedup_batched_mixed_vs_batched_fp32": res["batch_mixed"] / res["batch_fp32"],
+            "nmse_sample": {ws[q].name: v for q, v in nmse.items()},
+            "nmse_max_abs_diff_mixed_vs_fp32": max(diffs),
+            "iterations_per_instance_at_nmse": 8 + 2 * (warmup + steps) * iters}
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2005_09838_gb300 import build as _b
+    _b.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with ClockSampler(0) as clk:
-        for label, mixed in (("mixed", True), ("fp32", False)):
-            cs = contexts(mixed)
-            with tc.Batch(cs, stream=sptr) as B:
-                B.iterate(2 * 4)  # tuning trials (two per candidate branch count), real iterations
-                ms = _timed(torch, stream, flush, lambda: B.iterate(iters), args.steps, args.warmup)
-                res[f"batch_{label}"] = BATCH * iters * args.steps / (ms / 1e3)
-                res[f"branches_{label}"] = B.branches()
-            ms = _timed(torch, stream, flush, lambda: [c.iterate(iters, count=False) for c in cs], args.steps,
-                        args.warmup)
-            res[f"sequential_{label}"] = BATCH * iters * args.steps / (ms / 1e3)
-            for c in cs:
-                c.close()
-            torch.cuda.synchronize()
-    value = res["batch_mixed"]
+        res = batched_form(torch, dev, stream, flush, args.steps, args.warmup)
+    value = res["instance_iters_per_s"]["batch_mixed"]
     line = {"metric": "instance-iterations/s, batched form (64 heterogeneous completions, one graph launch per "
                       "iteration, TF32 tensor cores where r > 16)",
             "value": value, "unit": "instance-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": BATCH * iters * 1e3 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "tf32 (split operands, r > 16) / f32", "data": "synthetic",
-            "config": {"workload": "64 traffic tensors, n1 64-1024, n2 96-288, n3 28-168, r 4-32, 10-60% observed",
-                       "instances": [w.name for w in ws], "iters_per_step": iters, "entries_total": entries,
-                       "entries_per_s": value * entries / BATCH, "l2": "flushed before every timed step"},
-            "rates": res, "speedup_vs_sequential_fp32": value / res["sequential_fp32"],
-            "speedup_vs_batched_fp32": value / res["batch_fp32"], "clocks": clk.summary()}
+            "ms_per_step": BATCH * res["iters_per_step"] * 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32 (split operands, r > 16) / f32",
+            "data": "synthetic",
+            "config": {"workload": res["workload"], "instances": res["instances"],
+                       "iters_per_step": res["iters_per_step"], "entries_total": res["entries_total"],
+                       "entries_per_s": value * res["entries_total"] / BATCH,
+                       "l2": "flushed before every timed step"},
+            "rates": res["instance_iters_per_s"], "speedup_vs_sequential_fp32":
+                res["speedup_batched_mixed_vs_sequential_fp32"],
+            "speedup_vs_batched_fp32": res["speedup_batched_mixed_vs_batched_fp32"],
+            "nmse_max_abs_diff_mixed_vs_fp32": res["nmse_max_abs_diff_mixed_vs_fp32"], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 

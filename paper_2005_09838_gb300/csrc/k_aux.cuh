@@ -121,42 +121,69 @@ __global__ void k_check(Dev<T> d) {
   }
 }
 
-// rho1 term of f0 per slice: tr((X~^H H^T H X~)(Y~ Y~^H)) in FP64.
+// rho1 term of f0 per slice, tr(B A) with B = (H X~)^H (H X~) and A = Y~ Y~^H
+// (||H Z~_k||_F^2 for Z~_k = X~_k Y~_k, Eq. (HunfZ2)).  One CTA per slice; each
+// upper-triangle pair (s, u) of the two r x r Grams is summed by tp adjacent
+// threads that split the rows, with products in the working precision
+// accumulated error-free (dot2: about twice the working precision) and the
+// partial sums combined in FP64; the trace is accumulated in FP64 as
+// sum_s B_ss A_ss + 2 sum_{s<u} Re(B_su A_us).
 template <typename T>
-__global__ void k_rho1_term(Dev<T> d) {
+__device__ __forceinline__ void cdot2_acc(T (&acc)[4], cx<T> a, cx<T> b) {
+  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br), four error-free running sums
+  dot2(acc[0], acc[2], a.re, b.re);
+  dot2(acc[0], acc[2], a.im, b.im);
+  dot2(acc[1], acc[3], a.re, b.im);
+  dot2(acc[1], acc[3], -a.im, b.re);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rho1_term(Dev<T> d) {
   __shared__ double part[32];
   const int k = blockIdx.x;
   const int n1 = d.n1, n2 = d.n2, r = d.r;
+  const int ntask = r * (r + 1) / 2;
   const cx<T>* X = d.Xt + (size_t)k * r * n1;
   const cx<T>* Y = d.Yt + (size_t)k * r * n2;
+  int tp = 1;
+  while (tp < 32 && tp * 2 * ntask <= (int)blockDim.x) tp *= 2;
+  const int per_pass = blockDim.x / tp, q = threadIdx.x & (tp - 1);
   double tot = 0.0;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int s = e / r, u = e - s * r;
-    double hre = 0.0, him = 0.0;  // (HX)^H (HX) [s][u]
-    for (int i = 0; i + 1 < n1; ++i) {
-      const cx<T> a0 = X[(size_t)s * n1 + i], a1 = X[(size_t)s * n1 + i + 1];
-      const cx<T> b0 = X[(size_t)u * n1 + i], b1 = X[(size_t)u * n1 + i + 1];
-      const double ar = (double)a0.re - (double)a1.re, ai = (double)a0.im - (double)a1.im;
-      const double br = (double)b0.re - (double)b1.re, bi = (double)b0.im - (double)b1.im;
-      hre += ar * br + ai * bi;
-      him += ar * bi - ai * br;
+  for (int base = 0; base < ntask; base += per_pass) {  // every thread runs the same passes
+    const int task = base + (int)threadIdx.x / tp;
+    double bre = 0.0, bim = 0.0, are = 0.0, aim = 0.0;
+    int s = 0, u = 0;
+    if (task < ntask) {
+      tri_index(task, r, s, u);
+      T b[4] = {T(0), T(0), T(0), T(0)}, a[4] = {T(0), T(0), T(0), T(0)};
+      const cx<T>* xs = X + (size_t)s * n1;
+      const cx<T>* xu = X + (size_t)u * n1;
+      for (int i = q; i + 1 < n1; i += tp) cdot2_acc(b, xs[i] - xs[i + 1], xu[i] - xu[i + 1]);  // B_su
+      const cx<T>* ys = Y + (size_t)s * n2;
+      const cx<T>* yu = Y + (size_t)u * n2;
+      for (int j = q; j < n2; j += tp) cdot2_acc(a, ys[j], yu[j]);  // conj(y_s) y_u summed: A_us
+      bre = (double)b[0] + (double)b[2];
+      bim = (double)b[1] + (double)b[3];
+      are = (double)a[0] + (double)a[2];
+      aim = (double)a[1] + (double)a[3];
     }
-    double yre = 0.0, yim = 0.0;  // (Y Y^H)[u][s]
-    for (int j = 0; j < n2; ++j) {
-      const cx<T> a = Y[(size_t)u * n2 + j], b = Y[(size_t)s * n2 + j];
-      yre += (double)a.re * (double)b.re + (double)a.im * (double)b.im;
-      yim += (double)a.im * (double)b.re - (double)a.re * (double)b.im;
+    for (int o = tp >> 1; o > 0; o >>= 1) {
+      bre += __shfl_xor_sync(0xffffffffu, bre, o);
+      bim += __shfl_xor_sync(0xffffffffu, bim, o);
+      are += __shfl_xor_sync(0xffffffffu, are, o);
+      aim += __shfl_xor_sync(0xffffffffu, aim, o);
     }
-    tot += hre * yre - him * yim;
+    // B_su = sum_i conj(Hx_s) Hx_u = (bre, bim); A_us = sum_j y_u conj(y_s) = (are, aim)
+    if (task < ntask && q == 0) tot += (s == u ? 1.0 : 2.0) * (bre * are - bim * aim);
   }
   tot = warp_sum(tot);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) part[wid] = tot;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-    d.part_k[k] = s;
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += part[w];
+    d.part_k[k] = sum;
   }
 }
 

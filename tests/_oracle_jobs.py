@@ -43,3 +43,30 @@ def start_c2_trajectories(observed_list, iters, setting):
             else:
                 os.environ[k] = v
     return pool, futs
+
+
+def c4_inputs():
+    """The 529 x 288 x 168 differentiation workload (r = 16, 20% observed) in
+    FP32-representable values, and seeded initial factors X ~ N(0,1), Y = Y0."""
+    import workloads as wl
+    w = wl.c4(0.2)
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    rng = np.random.default_rng(w.seed + 17)
+    X = rng.standard_normal((w.n1, w.r, w.n3)).astype(np.float32).astype(np.float64)
+    return w, inst, X
+
+
+def _c4_loss_grad(rho1: float):
+    from oracle import method as O
+    w, inst, X = c4_inputs()
+    Y = inst["Y0"]
+    f = O.factor_loss(X, Y, inst["G"], inst["mask"], rho1)
+    gX, gY = O.factor_loss_grad(X, Y, inst["G"], inst["mask"], rho1)
+    return {"f": f, "gX": gX, "gY": gY}
+
+
+def start_c4_loss_grad(rho1: float):
+    """The oracle's loss and gradients of the differentiation form at the C4
+    initial factors, in one spawned worker; returns (pool, future)."""
+    pool = concurrent.futures.ProcessPoolExecutor(max_workers=1, mp_context=multiprocessing.get_context("spawn"))
+    return pool, pool.submit(_c4_loss_grad, rho1)

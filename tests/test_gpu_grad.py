@@ -15,6 +15,9 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp32": 1e-5}
 
 
+C4_RHO1 = 1e-3
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     import torch
@@ -22,6 +25,16 @@ def _built():
         pytest.skip("no CUDA device")
     from paper_2005_09838_gb300 import build
     build.build()
+
+
+@pytest.fixture(scope="module")
+def c4_oracle():
+    # the oracle's loss and gradients at the 529 x 288 x 168 initial factors, in a
+    # spawned worker (about a minute of CPU work)
+    import _oracle_jobs
+    pool, fut = _oracle_jobs.start_c4_loss_grad(C4_RHO1)
+    yield fut
+    pool.shutdown(cancel_futures=True)
 
 
 def _rel(a, b):
@@ -119,4 +132,36 @@ def test_autograd_function_and_block_gradient_descent():
                                              1.0 / Ly, 1.0 / Lx)
     assert all(b < a for a, b in zip(hist, hist[1:]))
     assert hist[-1] < 0.5 * hist[0]
+    g.close()
+
+
+def test_differentiation_form_c4_first_evaluation_and_block_descent(c4_oracle):
+    # the differentiation form's own workload: 529 x 288 x 168, r = 16, 20%
+    # observed, FP32.  The loss and both gradients at the initial factors against
+    # the oracle; then block gradient descent through torch.autograd, whose loss
+    # falls at every accepted block step
+    import torch
+    import _oracle_jobs
+    from paper_2005_09838_gb300 import autograd as ag
+    w, inst, X = _oracle_jobs.c4_inputs()
+    Y = inst["Y0"]
+    g = ag.grad_context(inst["G"], inst["mask"], w.r, C4_RHO1, dtype=torch.float32)
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda", requires_grad=True)
+    Yt = torch.tensor(Y, dtype=torch.float32, device="cuda", requires_grad=True)
+    loss = ag.factor_loss(Xt, Yt, g)
+    loss.backward()
+    ref = c4_oracle.result()
+    err_f = abs(float(loss.detach()) - ref["f"]) / ref["f"]
+    err_x = _rel(Xt.grad.cpu().numpy().astype(np.float64), ref["gX"])
+    err_y = _rel(Yt.grad.cpu().numpy().astype(np.float64), ref["gY"])
+    print(f"C4 loss {err_f:.2e}, dL/dX {err_x:.2e}, dL/dY {err_y:.2e}")
+    assert err_f <= TOL["fp32"]
+    assert err_x <= TOL["fp32"]
+    assert err_y <= TOL["fp32"]
+    # steps from 1/L of the initial factors (L over the slices of the block's Gram)
+    Xf, Yf = np.fft.fft(X, axis=2), np.fft.fft(Y, axis=2)
+    Ly = max(np.linalg.norm(Yf[:, :, k] @ Yf[:, :, k].conj().T, 2) for k in range(w.n3))
+    Lx = max(np.linalg.norm(Xf[:, :, k].conj().T @ Xf[:, :, k], 2) for k in range(w.n3))
+    X1, Y1, hist = ag.block_gradient_descent(g, Xt.detach(), Yt.detach(), 2, 1.0 / Ly, 1.0 / Lx)
+    assert all(b < a for a, b in zip(hist, hist[1:]))
     g.close()
