@@ -34,7 +34,10 @@ Readings taken where the paper is silent (listed in the design notes too):
   h_k); ``step="scaled"`` uses fixed user alpha, beta divided by L_k1, L_k2.
 * pseudo-inverse cutoff: eigenvalues lambda <= rtol * lambda_max of the
   Hermitian PSD Gram are treated as zero; rtol defaults to r * 2**-52.
-* rank vector (step 5): fixed r for every slice.
+* rank vector (step 5): fixed r for every slice in ``tctf2r``;
+  ``tctf2r_rank`` carries out step 5 as a rank decrease: a slice drops the
+  directions whose Y-step Gram eigenvalue stayed at or below
+  rank_tol * lambda_max for ``patience`` consecutive iterations.
 * initial point: W0 = P_Omega(G), X0 given (default 0), Y0 given.
 * DFT sign: the paper's omega = exp(+2 pi i / m3); ``sign=-1`` gives the
   other convention (every real output is the same).
@@ -414,6 +417,91 @@ def tctf2r(G, mask, r, mu, rho1, rho2, Y0, X0=None, iters=10, step="exact",
     if record:
         out["hist"] = hist
     return out
+
+
+# ---------------------------------------------------------------------------
+# Step 5 of the TCTF2R Algorithm: the rank vector (reading of this build)
+# ---------------------------------------------------------------------------
+
+def rank_adjust_slice(Xk, Yk, rho1, tol):
+    """One rank decrease of slice k (step 5 reading): the eigendecomposition
+    G = V diag(lambda) V^* of G = X~_k^* H_rho1 X~_k; the directions with
+    lambda <= tol * lambda_max are dropped, X~_k <- X~_k V_keep and
+    Y~_k <- V_keep^* Y~_k (the sizes of X~_k and Y~_k shrink to the kept count).
+    Returns (X, Y, dropped)."""
+    m1 = Xk.shape[0]
+    Gx = Xk.conj().T @ H_rho(m1, rho1) @ Xk
+    lam, V = np.linalg.eigh(0.5 * (Gx + Gx.conj().T))
+    lmax = float(lam.max()) if lam.size else 0.0
+    keep = lam > tol * lmax
+    if keep.all() or not keep.any():
+        return Xk, Yk, 0
+    Vk = V[:, keep]
+    return Xk @ Vk, Vk.conj().T @ Yk, int((~keep).sum())
+
+
+def tctf2r_rank(G, mask, r, mu, rho1, rho2, Y0, X0=None, iters=10, rank_tol=0.0, patience=1, rtol=None,
+                sign=+1):
+    """The TCTF2R Algorithm with step 5 carried out (exact steps).
+
+    Reading of step 5 ("adjust the rank vector and the sizes of X~_k, Y~_k"):
+    after the W-update of iteration l, every solved slice k checks the
+    eigenvalues of its Y-step Gram G_k = X~_k^* H_rho1 X~_k; when at least one
+    of them has been <= rank_tol * lambda_max(G_k) for ``patience`` consecutive
+    iterations, those directions are dropped (rank_adjust_slice) and the count
+    restarts.  W~ is not changed by the step.  Slices k > floor(m3/2) follow
+    by the conjugate relation, so r_k = r_{m3-k+2}.  The factors are kept as
+    one matrix per slice, of width r_k.
+
+    Returns a dict with W, f0 (the objective of the final iterate) and the
+    rank vector of all m3 slices."""
+    G = np.asarray(G, dtype=np.float64)
+    mask = np.asarray(mask, dtype=bool)
+    m1, m2, m3 = G.shape
+    S = m3 // 2 + 1
+    X0 = np.zeros((m1, r, m3)) if X0 is None else np.asarray(X0, np.float64)
+    W = np.where(mask, G, 0.0)
+    Wt = dft3(W, sign=sign)
+    X0t, Y0t = dft3(X0, sign=sign), dft3(np.asarray(Y0, np.float64), sign=sign)
+    Xs = [X0t[:, :, k].copy() for k in range(S)]
+    Ys = [Y0t[:, :, k].copy() for k in range(S)]
+    count = [0] * S
+    for _ in range(iters):
+        for k in range(S):                                            # step 1
+            Xs[k] = x_update(Xs[k], Ys[k], Wt[:, :, k], rho1, rtol=rtol)
+        for k in range(S):                                            # step 2
+            Ys[k] = y_update(Xs[k], Ys[k], Wt[:, :, k], rho1, rtol=rtol)
+        Zt = np.zeros((m1, m2, m3), dtype=np.complex128)              # step 3
+        for k in range(S):
+            Zt[:, :, k] = Xs[k] @ Ys[k]
+        Zt = mirror_half(Zt[:, :, :S], m3)
+        Z = idft3(Zt, sign=sign).real
+        W = w_step_kkt(Z, G, mask, mu, rho2)                          # step 4
+        if rank_tol > 0:                                              # step 5
+            for k in range(S):
+                m = Xs[k].shape[0]
+                Gx = Xs[k].conj().T @ H_rho(m, rho1) @ Xs[k]
+                lam = np.linalg.eigvalsh(0.5 * (Gx + Gx.conj().T))
+                small = lam.size > 1 and bool(np.any(lam <= rank_tol * lam.max()))
+                count[k] = count[k] + 1 if small else 0
+                if count[k] >= patience:
+                    Xs[k], Ys[k], _ = rank_adjust_slice(Xs[k], Ys[k], rho1, rank_tol)
+                    count[k] = 0
+        Wt = dft3(W, sign=sign)                                       # step 7
+    ranks = [Xs[k].shape[1] for k in range(S)]
+    full = ranks + [ranks[m3 - k] for k in range(S, m3)]
+    # f0 of the final iterate: X*Y from the slices (mirrored), W
+    Zt = np.zeros((m1, m2, m3), dtype=np.complex128)
+    for k in range(S):
+        Zt[:, :, k] = Xs[k] @ Ys[k]
+    Z = idft3(mirror_half(Zt[:, :, :S], m3), sign=sign).real
+    Hd, Kd = toeplitz_D(m1), toeplitz_D(m2)
+    f = 0.5 * np.sum((Z - W) ** 2) + 0.5 * mu * np.sum(W ** 2)
+    if m1 > 1:
+        f += 0.5 * rho1 * np.sum((Hd @ unfold(Z, 1)) ** 2)
+    if m2 > 1:
+        f += 0.5 * rho2 * np.sum((Kd @ unfold(W, 2)) ** 2)
+    return {"W": W, "Z": Z, "f0": float(f), "ranks": full}
 
 
 # ---------------------------------------------------------------------------
