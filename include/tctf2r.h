@@ -164,6 +164,28 @@ tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
  * TC_ERR_CUDA. */
 tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* iters_run);
 
+/* Step 5 of the TCTF2R Algorithm (Sec. 4.1): "adjust the rank vector and the
+ * sizes of X~_k and Y~_k".  The paper leaves the rule open; this library reads
+ * it as a rank decrease.  After the W-update of each iteration every solved
+ * slice k takes the eigendecomposition of its Y-step Gram
+ * G_k = X~_k^* H_rho1 X~_k; while at least one eigenvalue of its active
+ * directions is <= tol * lambda_max(G_k) a per-slice count grows (else it
+ * restarts), and when the count reaches patience the slice keeps only the
+ * directions above that level (X~_k <- X~_k V_keep, Y~_k <- V_keep^* Y~_k) and
+ * its rank r_k shrinks.  W~ is not changed by the step.  Slices past
+ * floor(n3/2) follow by conjugate symmetry, so r_k = r_{n3-k+2} (1-based).
+ * The initial rank vector is r for every slice; ranks never grow.
+ * tc_rank_rule: tol in [0, 1) (0 turns the rule off for the following
+ *   iterations; the ranks reached so far stay), patience >= 1.  Recaptures the
+ *   iteration graph and synchronises the stream; set it before adding the
+ *   context to a batch (a batch holds the graph captured at tc_batch_create).
+ *   Errors: TC_ERR_ARG, TC_ERR_NOMEM, TC_ERR_CUDA, TC_ERR_STATE.
+ * tc_ranks: ranks receives n3 values, the rank of every frontal slice of the
+ *   DFT (r for all while the rule has never been on).  Synchronises the stream.
+ *   Errors: TC_ERR_ARG, TC_ERR_CUDA, TC_ERR_STATE. */
+tc_status tc_rank_rule(tc_ctx* c, double tol, int32_t patience);
+tc_status tc_ranks(tc_ctx* c, int32_t* ranks);
+
 /* Batched form: many independent completions (contexts of any sizes and either
  * precision, on the current device) advanced together, one CUDA graph launch
  * per iteration.  The graph holds each instance's captured iteration in K

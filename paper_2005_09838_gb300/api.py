@@ -21,14 +21,16 @@ def _from_colmajor(flat: np.ndarray, shape) -> np.ndarray:
 
 def complete(G, mask, Y0, r, iters, mu=0.0, rho1=0.0, rho2=0.0, precision="fp32", X0=None,
              want_factors=False, objective=True, step="exact", alpha=1.0, beta=1.0, eps=0.0,
-             single_pass=False):
+             single_pass=False, rank_tol=0.0, rank_patience=1):
     """Run up to ``iters`` TCTF2R iterations on the GPU (fewer when ``eps`` > 0
     and the stopping test holds).  Returns a dict with W (and X, Y spatial with
     ``want_factors``), f0, resid_obs, the iterations run and, with ``eps`` > 0,
     the last changes (||dX~||_inf, ||dY~||_inf, ||dW||_F).  ``precision`` is
     "fp64", "fp32", or the precision form "tf32" / "bf16" (float data; see
     tc_precision in the C header), where ``single_pass`` rounds the tensor-core
-    operands once instead of splitting them."""
+    operands once instead of splitting them.  ``rank_tol`` > 0 turns on step 5
+    of the Algorithm (tc_rank_rule) with ``rank_patience``; the result then
+    holds the final rank vector under "ranks"."""
     prec = {"fp32": tc.TC_FP32, "fp64": tc.TC_FP64, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16}[precision]
     dt = np.float64 if prec == tc.TC_FP64 else np.float32
     n1, n2, n3 = G.shape
@@ -40,7 +42,11 @@ def complete(G, mask, Y0, r, iters, mu=0.0, rho1=0.0, rho2=0.0, precision="fp32"
     y = _colmajor(Y0, dt)
     x = None if X0 is None else _colmajor(X0, dt)
     with tc.Completion(p, g, m, y, x) as c:
+        if rank_tol > 0:
+            c.rank_rule(rank_tol, rank_patience)
         out = {"iters": c.iterate(iters)}
+        if rank_tol > 0:
+            out["ranks"] = c.ranks()
         if eps > 0:
             out["changes"], out["stopped"], out["iters_total"] = c.convergence()
         if objective:

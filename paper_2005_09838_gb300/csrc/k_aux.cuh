@@ -187,6 +187,177 @@ __global__ void __launch_bounds__(256) k_rho1_term(Dev<T> d) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Step 5 of the TCTF2R Algorithm: adjust the rank vector (the Algorithm leaves
+// the rule open; this library's reading).  After the W-update of an
+// iteration, every solved slice k takes the eigendecomposition G_k = V diag(lambda) V^*
+// of its Y-step Gram G_k = X~_k^* H_rho1 X~_k; while at least one eigenvalue of
+// the slice's active directions is <= rank_tol lambda_max, a counter grows
+// (else it restarts), and when it reaches rank_patience the slice keeps only
+// the directions above that level: X~_k <- X~_k V_keep and Y~_k <- V_keep^* Y~_k,
+// ordered by decreasing eigenvalue, the rest of the r columns / rows set to
+// zero (r_k shrinks; slices past floor(n3/2) follow by conjugate symmetry).
+// W~ does not change: the part of Z~_k = X~_k Y~_k that is dropped,
+// dZ = sum_d (X~_k v_d)(v_d^* Y~_k), moves from the stored Z~ to the residual
+// R~ = W~ - Z~.  Zero columns stay zero through the updates (their Gram rows
+// and columns are exactly zero and the pseudo-inverse cuts them).
+// One CTA per slice; G is summed error-free in the working precision (FP64
+// values) and its eigendecomposition is the block Jacobi in FP64.  Shared
+// memory: rank_smem_bytes(r).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t rank_smem_bytes(int r) {
+  return (7 * (size_t)r * r + 3 * (size_t)r + 2) * sizeof(cx<double>) + 2 * 32 * sizeof(int);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rank(Dev<T> d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (converged(d)) return;
+  const int k = blockIdx.x, n1 = d.n1, n2 = d.n2, r = d.r, rr = r * r;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  cx<double>* Gm = reinterpret_cast<cx<double>*>(smem);
+  cx<double>* Ap = Gm + rr;
+  cx<double>* P = Ap + rr;
+  cx<double>* V = P + rr;
+  cx<double>* Wk = V + rr;  // 2 r^2
+  cx<double>* piv = Wk + 2 * rr;  // 3 r
+  double* lmx = reinterpret_cast<double*>(piv + 3 * r);  // 2
+  int* perm = reinterpret_cast<int*>(lmx + 4);            // [32] kept then dropped directions
+  int* ctl = perm + 32;                                   // [0] directions kept (0: no change)
+  const bool realslice = (k == 0) || (2 * k == d.n3);
+  const double rho1 = (double)d.rho1;
+  cx<T>* X = d.Xt + (size_t)k * r * n1;
+  cx<T>* Y = d.Yt + (size_t)k * r * n2;
+  // ---- G = X~^* X~ + rho1 (H X~)^* (H X~), upper triangle, error-free sums --------------
+  {
+    const int ntask = r * (r + 1) / 2;
+    int tp = 1;
+    while (tp < 32 && tp * 2 * ntask <= nt) tp *= 2;
+    const int per_pass = nt / tp, q = tid & (tp - 1);
+    for (int base = 0; base < ntask; base += per_pass) {
+      const int task = base + tid / tp;
+      double re = 0.0, im = 0.0;
+      int s = 0, u = 0;
+      if (task < ntask) {
+        tri_index(task, r, s, u);
+        T a[4] = {T(0), T(0), T(0), T(0)}, h[4] = {T(0), T(0), T(0), T(0)};
+        const cx<T>* xs = X + (size_t)s * n1;
+        const cx<T>* xu = X + (size_t)u * n1;
+        for (int i = q; i < n1; i += tp) {
+          cdot2_acc(a, xs[i], xu[i]);
+          if (i + 1 < n1) cdot2_acc(h, xs[i] - xs[i + 1], xu[i] - xu[i + 1]);
+        }
+        re = ((double)a[0] + (double)a[2]) + rho1 * ((double)h[0] + (double)h[2]);
+        im = ((double)a[1] + (double)a[3]) + rho1 * ((double)h[1] + (double)h[3]);
+      }
+      for (int o = tp >> 1; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (task < ntask && q == 0) {
+        if (s == u || realslice) im = 0.0;
+        Gm[s * r + u] = cx<double>{re, im};
+        Gm[u * r + s] = cx<double>{re, -im};
+      }
+    }
+  }
+  __syncthreads();
+  // ---- eigendecomposition: eigenvalues on the diagonal of Wk, eigenvectors in V --------
+  block_jacobi_pinv<double>(Gm, Ap, P, V, Wk, piv, r, 0.0, lmx);
+  __syncthreads();
+  if (tid == 0) {
+    const int ra = d.rk[k];
+    const double lmax = lmx[0];
+    int nsmall = 0;
+    for (int c = 0; c < r; ++c) nsmall += (Wk[c * r + c].re <= d.rank_tol * lmax) ? 1 : 0;
+    // the r - ra inactive directions have eigenvalue 0 exactly
+    const bool small = lmax > 0.0 && ra > 1 && nsmall > r - ra;
+    int cnt = small ? d.rcnt[k] + 1 : 0;
+    int keep = 0;
+    if (cnt >= d.rank_patience && small) {
+      // kept directions by decreasing eigenvalue, then the dropped ones
+      bool used[32] = {};
+      for (int c = 0; c < r; ++c) {
+        int best = -1;
+        for (int e = 0; e < r; ++e)
+          if (!used[e] && (best < 0 || Wk[e * r + e].re > Wk[best * r + best].re)) best = e;
+        used[best] = true;
+        perm[c] = best;
+        if (Wk[best * r + best].re > d.rank_tol * lmax) ++keep;
+      }
+      cnt = 0;
+      d.rk[k] = keep;
+    }
+    d.rcnt[k] = cnt;
+    ctl[0] = keep;
+  }
+  __syncthreads();
+  const int keep = ctl[0];
+  if (keep == 0) return;
+  const int nd = r - keep;
+  // ---- dropped part of Z~_k: a_d = X~ v_d (n1), b_d = v_d^* Y~ (n2), before rotating ----
+  cx<T>* ad = d.rscr + (size_t)k * r * (n1 + n2);
+  cx<T>* bd = ad + (size_t)r * n1;
+  for (int e = tid; e < nd * n1; e += nt) {
+    const int dd = e / n1, i = e - dd * n1, v = perm[keep + dd];
+    cx<double> acc = {0.0, 0.0};
+    for (int u = 0; u < r; ++u) {
+      const cx<T> x = X[(size_t)u * n1 + i];
+      acc = acc + cmul(cx<double>{(double)x.re, (double)x.im}, V[u * r + v]);
+    }
+    ad[(size_t)dd * n1 + i] = cx<T>{(T)acc.re, (T)acc.im};
+  }
+  for (int e = tid; e < nd * n2; e += nt) {
+    const int dd = e / n2, j = e - dd * n2, v = perm[keep + dd];
+    cx<double> acc = {0.0, 0.0};
+    for (int u = 0; u < r; ++u) {
+      const cx<T> y = Y[(size_t)u * n2 + j];
+      acc = acc + cmulc(cx<double>{(double)y.re, (double)y.im}, V[u * r + v]);  // conj(V_uv) y
+    }
+    bd[(size_t)dd * n2 + j] = cx<T>{(T)acc.re, (T)acc.im};
+  }
+  __syncthreads();
+  // ---- rotate: X~ <- X~ V_perm (kept columns, the rest zero), Y~ <- V_perm^* Y~ ---------
+  for (int i = tid; i < n1; i += nt) {
+    cx<double> x[kMaxRank];
+    for (int u = 0; u < r; ++u) {
+      const cx<T> v = X[(size_t)u * n1 + i];
+      x[u] = cx<double>{(double)v.re, (double)v.im};
+    }
+    for (int c = 0; c < r; ++c) {
+      cx<double> acc = {0.0, 0.0};
+      if (c < keep)
+        for (int u = 0; u < r; ++u) acc = acc + cmul(x[u], V[u * r + perm[c]]);
+      if (realslice) acc.im = 0.0;
+      X[(size_t)c * n1 + i] = cx<T>{(T)acc.re, (T)acc.im};
+    }
+  }
+  for (int j = tid; j < n2; j += nt) {
+    cx<double> y[kMaxRank];
+    for (int u = 0; u < r; ++u) {
+      const cx<T> v = Y[(size_t)u * n2 + j];
+      y[u] = cx<double>{(double)v.re, (double)v.im};
+    }
+    for (int c = 0; c < r; ++c) {
+      cx<double> acc = {0.0, 0.0};
+      if (c < keep)
+        for (int u = 0; u < r; ++u) acc = acc + cmulc(y[u], V[u * r + perm[c]]);
+      if (realslice) acc.im = 0.0;
+      Y[(size_t)c * n2 + j] = cx<T>{(T)acc.re, (T)acc.im};
+    }
+  }
+  // ---- W~ unchanged: R~ += dZ, Z~ -= dZ on slice k ------------------------------------
+  for (size_t e = tid; e < (size_t)n1 * n2; e += nt) {
+    const int i = (int)(e / n2), j = (int)(e - (size_t)i * n2);
+    cx<T> dz = {T(0), T(0)};
+    for (int dd = 0; dd < nd; ++dd) cfma(dz, ad[(size_t)dd * n1 + i], bd[(size_t)dd * n2 + j]);
+    if (realslice) dz.im = T(0);
+    const size_t o = ((size_t)i * d.S + k) * n2 + j;
+    d.Rt[o] = d.Rt[o] + dz;
+    d.Zt[o] = d.Zt[o] - dz;
+  }
+}
+
 // Initial Z~ = X~Y~ (step 3 at the initial point; during the iteration the
 // Y-step kernel writes Z~).  One thread per output.
 template <typename T>

@@ -992,15 +992,18 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
   // FP64 Gauss-Jordan on the real Gram, accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
   // (then lambda_min > rtol lambda_max: nothing is cut, G^+ = G^-1); otherwise the
   // eigendecomposition fallback applies the cutoff
-  double* g = reinterpret_cast<double*>(Ap64);      // r^2 real values of G
-  double* wk = reinterpret_cast<double*>(W64);      // 2 r^2
+  // With the rank rule on (step 5), only the leading ra x ra block is active: the
+  // other rows and columns of G are zero, and so are those of G^+.
+  const int ra = d.rk ? d.rk[k] : r, ra2 = ra * ra;
+  double* g = reinterpret_cast<double*>(Ap64);      // ra^2 real values of G (compact)
+  double* wk = reinterpret_cast<double*>(W64);      // 2 ra^2
   double* pv = reinterpret_cast<double*>(piv64);    // 2
-  for (int e = tid; e < rr; e += nt) g[e] = G64[e].re;
+  for (int e = tid; e < ra2; e += nt) g[e] = G64[(e / ra) * r + e % ra].re;
   __syncthreads();
-  int ok = real_gj_fp64(g, wk, pv, r);
+  int ok = real_gj_fp64(g, wk, pv, ra);
   if (tid < 32) {
     double an = 0.0, in = 0.0;
-    for (int e = tid; e < rr; e += 32) {
+    for (int e = tid; e < ra2; e += 32) {
       an += g[e] * g[e];
       in += wk[e] * wk[e];
     }
@@ -1010,10 +1013,9 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
   }
   __syncthreads();
   if (sred[1] != 0.0) {
-    for (int e = tid; e < rr; e += nt) {
+    for (int e = tid; e < rr; e += nt) {  // g (aliasing Ap64) is no longer read
       const int i = e / r, j = e - i * r;
-      const double v = 0.5 * (wk[i * r + j] + wk[j * r + i]);
-      Ap64[e] = cx<double>{v, 0.0};  // g (aliasing Ap64) is no longer read
+      Ap64[e] = cx<double>{(i < ra && j < ra) ? 0.5 * (wk[i * ra + j] + wk[j * ra + i]) : 0.0, 0.0};
     }
   } else {
     jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);

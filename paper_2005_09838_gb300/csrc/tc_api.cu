@@ -13,6 +13,7 @@
 struct tc_ctx {
   tc::EngineBase* eng = nullptr;
   int device = 0;
+  int64_t n3 = 0;
 };
 
 namespace {
@@ -73,6 +74,7 @@ tc_status tc_init(tc_ctx** out, const tc_params* p, const void* G, const uint8_t
   if (!G || !mask || !Y0) return fail(TC_ERR_ARG, "G, mask and Y0 are required");
   tc_ctx* c = new (std::nothrow) tc_ctx();
   if (!c) return fail(TC_ERR_NOMEM, "host allocation failed");
+  c->n3 = p->n3;
   c->eng = (p->precision == TC_FP64) ? tc::make_engine_f64() : tc::make_engine_f32();
   if (!c->eng) {
     delete c;
@@ -159,6 +161,35 @@ tc_status tc_convergence(tc_ctx* c, double* changes, int32_t* stopped, int64_t* 
   if (stopped) *stopped = s;
   if (iters_run) *iters_run = it;
   return st == TC_OK ? st : fail(st, err);
+}
+
+tc_status tc_rank_rule(tc_ctx* c, double tol, int32_t patience) {
+  g_last_error.clear();
+  if (!c) return fail(TC_ERR_ARG, "ctx is required");
+  if (!(tol >= 0.0) || !(tol < 1.0)) return fail(TC_ERR_ARG, "tol must satisfy 0 <= tol < 1");
+  if (patience < 1) return fail(TC_ERR_ARG, "patience must be >= 1");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  std::string err;
+  tc_status st = c->eng->set_rank_rule(tol, patience, err);
+  if (prev != c->device) cudaSetDevice(prev);
+  return st == TC_OK ? st : fail(st, err);
+}
+
+tc_status tc_ranks(tc_ctx* c, int32_t* ranks) {
+  g_last_error.clear();
+  if (!c || !ranks) return fail(TC_ERR_ARG, "ctx and ranks are required");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  std::string err;
+  std::vector<int> h((size_t)c->n3);
+  tc_status st = c->eng->ranks(h.data(), err);
+  if (prev != c->device) cudaSetDevice(prev);
+  if (st != TC_OK) return fail(st, err);
+  for (size_t k = 0; k < h.size(); ++k) ranks[k] = (int32_t)h[k];
+  return TC_OK;
 }
 
 // ---------------------------------------------------------------------------

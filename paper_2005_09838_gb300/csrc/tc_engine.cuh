@@ -644,14 +644,19 @@ class Engine final : public EngineBase {
       launch_slab(MODE_ITER, nullptr, 0, cap_stream_);
       le = cudaPeekAtLastError();
     }
+    if (forked) {
+      const cudaError_t je = cudaStreamWaitEvent(cap_stream_, ev_join_, 0);
+      if (le == cudaSuccess) le = je;
+    }
+    if (le == cudaSuccess && d_.rk) {
+      at = "rank";
+      launch_rank(cap_stream_);  // step 5, after the A^+ branch has joined
+      le = cudaPeekAtLastError();
+    }
     if (le == cudaSuccess && d_.conv) {
       at = "check";
       k_check<T><<<1, 32, 0, cap_stream_>>>(d_);
       le = cudaPeekAtLastError();
-    }
-    if (forked) {
-      const cudaError_t je = cudaStreamWaitEvent(cap_stream_, ev_join_, 0);
-      if (le == cudaSuccess) le = je;
     }
     cudaGetLastError();
     cudaError_t ce = cudaStreamEndCapture(cap_stream_, out);
@@ -664,6 +669,55 @@ class Engine final : public EngineBase {
     }
     return TC_OK;
   }
+  tc_status set_rank_rule(double tol, int patience, std::string& err) override {
+    if (poisoned_) {
+      err = "context poisoned by an earlier error";
+      return TC_ERR_STATE;
+    }
+    if (tol > 0.0 && !rk_) {
+      rk_ = alloc<int>((size_t)S_, err);
+      rcnt_ = alloc<int>((size_t)S_, err);
+      rscr_ = alloc<cx<T>>((size_t)S_ * r_ * (n1_ + n2_), err);
+      if (!err.empty()) return TC_ERR_NOMEM;
+      std::vector<int> full((size_t)S_, r_);
+      TC_CUDA_TRY(cudaMemcpyAsync(rk_, full.data(), full.size() * sizeof(int), cudaMemcpyHostToDevice, stream_));
+      TC_CUDA_TRY(cudaMemsetAsync(rcnt_, 0, (size_t)S_ * sizeof(int), stream_));
+      TC_CUDA_TRY(cudaStreamSynchronize(stream_));  // the host vector goes out of scope
+      rank_smem_ = rank_smem_bytes(r_);
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_rank<T>, rank_smem_));
+    }
+    d_.rk = tol > 0.0 ? rk_ : nullptr;
+    d_.rcnt = rcnt_;
+    d_.rscr = rscr_;
+    d_.rank_tol = tol;
+    d_.rank_patience = patience;
+    if (rcnt_) TC_CUDA_TRY(cudaMemsetAsync(rcnt_, 0, (size_t)S_ * sizeof(int), stream_));
+    // the captured iteration carries d_ by value: capture it again
+    if (graph_exec_) {
+      TC_CUDA_TRY(cudaStreamSynchronize(stream_));
+      cudaGraphExecDestroy(graph_exec_);
+      graph_exec_ = nullptr;
+    }
+    tc_status st = capture(err);
+    if (st != TC_OK) return st;
+    TC_CUDA_TRY(cudaGraphUpload(graph_exec_, stream_));
+    return TC_OK;
+  }
+
+  tc_status ranks(int* out, std::string& err) override {
+    if (poisoned_) {
+      err = "context poisoned by an earlier error";
+      return TC_ERR_STATE;
+    }
+    std::vector<int> h((size_t)S_, r_);
+    if (rk_) {
+      TC_CUDA_TRY(cudaMemcpyAsync(h.data(), rk_, h.size() * sizeof(int), cudaMemcpyDeviceToHost, stream_));
+      TC_CUDA_TRY(cudaStreamSynchronize(stream_));
+    }
+    for (int k = 0; k < n3_; ++k) out[k] = h[k < S_ ? k : n3_ - k];  // r_k = r_{n3-k} (conjugate slices)
+    return TC_OK;
+  }
+
   cudaStream_t stream() const override { return stream_; }
   bool poisoned() const override { return poisoned_; }
 
@@ -687,6 +741,7 @@ class Engine final : public EngineBase {
       cudaEventRecord(ev[3], stream_);
       launch_slab(MODE_ITER, nullptr, 0, stream_);
       cudaEventRecord(ev[4], stream_);
+      if (d_.rk) launch_rank(stream_);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
       for (int q = 0; q < K && e == cudaSuccess; ++q) {
@@ -761,11 +816,20 @@ class Engine final : public EngineBase {
 
   // One TCTF2R iteration: Q = R~Y~^H, X-step (+ Y-step r x r work), Y-step,
   // then the slab kernel (Z, W-step, R~).
+  // Step 5 (rank vector): the rank kernel, then the tile Grams of Y~ and A^+ of
+  // the next X-step again (the rank kernel may have rotated Y~).
+  void launch_rank(cudaStream_t s) {
+    k_rank<T><<<S_, 256, rank_smem_, s>>>(d_);
+    k_gram_tiles<T><<<dim3(S_, d_.ytiles), 256, 0, s>>>(d_);
+    if (xsplit_ || apre_) xa_fn_<<<S_, xa_threads_, xa_smem_, s>>>(d_);
+  }
+
   void launch_iteration(cudaStream_t s) {
     launch_qcon(s);
     launch_xstep(s);
     launch_ystep(s);
     launch_slab(MODE_ITER, nullptr, 0, s);
+    if (d_.rk) launch_rank(s);
     if (d_.conv) k_check<T><<<1, 32, 0, s>>>(d_);  // step 6
   }
 
@@ -814,6 +878,10 @@ class Engine final : public EngineBase {
   bool mixed_ = false;
   bool xsplit_ = false;  // X-step as four kernels
   bool apre_ = false;    // one-CTA X-step with A^+ from k_xa on a graph branch
+  int* rk_ = nullptr;    // step 5: slice ranks, counters and work (allocated when the rule is first on)
+  int* rcnt_ = nullptr;
+  cx<T>* rscr_ = nullptr;
+  size_t rank_smem_ = 0;
   int xa_threads_ = kXaThreads;
   YFn<T> xa_fn_ = nullptr, xc_fn_ = nullptr;
   int gch_ = 0;

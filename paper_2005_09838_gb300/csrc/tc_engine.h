@@ -20,6 +20,9 @@ struct EngineBase {
   virtual tc_status result(void* W, void* X, void* Y, bool on_device, std::string& err) = 0;
   virtual tc_status profile(int n, double* ms, std::string& err) = 0;
   virtual tc_status convergence(double* changes, int* stopped, long long* iters_run, std::string& err) = 0;
+  // step 5 (rank vector): tol = 0 turns the rule off; ranks gets n3 values
+  virtual tc_status set_rank_rule(double tol, int patience, std::string& err) = 0;
+  virtual tc_status ranks(int* out, std::string& err) = 0;
   virtual void release() = 0;
   // one iteration captured as a graph (the caller owns and destroys it)
   virtual tc_status capture_iteration(cudaGraph_t* out, std::string& err) = 0;

@@ -71,6 +71,12 @@ struct Dev {
   int gch;
   int apre;          // 1: A^+, P, certA, tstep of the one-CTA X-step come from k_xa (run on a
                      // graph branch after each Y-step) instead of being formed in k_xstep
+  // step 5 of the Algorithm (rank vector), when the rule is on (rk != nullptr)
+  int* rk;           // [S] rank of each solved slice: columns rk..r-1 of X~_k and rows of Y~_k are zero
+  int* rcnt;         // [S] consecutive iterations with a Gram eigenvalue at or below rank_tol lambda_max
+  cx<T>* rscr;       // [S][r][n1 + n2] work of k_rank (X~ v_d and v_d^H Y~ of the dropped directions)
+  double rank_tol;
+  int rank_patience;
 };
 
 // True once the stopping test has fired: the iteration kernels return at once.

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_ARG", 2: "TC_ERR_NOMEM", 3: "TC_ERR_CUDA"
 
 # Entry points declared in include/tctf2r.h (checked by the tests).
 EXPORTS = ("tc_init", "tc_iterate", "tc_objective", "tc_result", "tc_profile", "tc_free", "tc_last_error",
-           "tc_version")
+           "tc_version", "tc_rank_rule", "tc_ranks")
 
 
 class tc_params(ctypes.Structure):
@@ -76,6 +76,10 @@ def load(path: str | None = None):
     lib.tc_convergence.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
                                    ctypes.POINTER(ctypes.c_int64)]
     lib.tc_convergence.restype = ctypes.c_int
+    lib.tc_rank_rule.argtypes = [P, ctypes.c_double, ctypes.c_int32]
+    lib.tc_rank_rule.restype = ctypes.c_int
+    lib.tc_ranks.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.tc_ranks.restype = ctypes.c_int
     lib.tc_complete_static.argtypes = [ctypes.POINTER(tc_params), P, P, P, P, ctypes.c_int32, P,
                                        ctypes.POINTER(ctypes.c_double), P]
     lib.tc_complete_static.restype = ctypes.c_int
@@ -163,6 +167,18 @@ class Completion:
         it = ctypes.c_int64(0)
         _check(self._lib.tc_convergence(self._ctx, ch, ctypes.byref(stopped), ctypes.byref(it)))
         return tuple(ch), bool(stopped.value), int(it.value)
+
+    def rank_rule(self, tol: float, patience: int = 1):
+        """Step 5 of the Algorithm (tc_rank_rule): rank decrease of the slices whose
+        Y-step Gram has eigenvalues at or below tol * lambda_max for patience
+        consecutive iterations; tol = 0 turns it off."""
+        _check(self._lib.tc_rank_rule(self._ctx, float(tol), int(patience)))
+
+    def ranks(self):
+        """The rank of every frontal slice (n3 values, tc_ranks)."""
+        out = (ctypes.c_int32 * int(self.params.n3))()
+        _check(self._lib.tc_ranks(self._ctx, out))
+        return list(out)
 
     def objective(self):
         f0 = ctypes.c_double()
