@@ -19,12 +19,14 @@ enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2, MODE_GRAD = 3 };
 // on one scheduler and cap a thread at 168 registers); tubes beyond the thread
 // count loop.
 __host__ __device__ constexpr int slab_max_threads(int) { return 256; }
+// Rows (inverse) or slices (forward) per item of the generic transform.
+constexpr int kTL = 4;
 
 // Odd stride between tubes in the slab (n3 values per tube).
 __host__ __device__ inline int slab_stride(int n3) { return n3 | 1; }
 
 struct SlabLayout {
-  size_t wtab, red, msk, stw, spec, spat, total;  // byte offsets and total shared bytes
+  size_t wtab, red, msk, stw, tw, spec, spat, total;  // byte offsets and total shared bytes
   size_t slab_bytes;                         // bytes of the slab buffers per CTA
 };
 
@@ -41,6 +43,8 @@ __host__ __device__ inline SlabLayout slab_layout(int n2, int n3, bool specialis
   off = align_up(off + sizeof(uint32_t) * (size_t)n3 * ((n2 + 31) / 32), 16);
   L.stw = off;  // per row and mask word: start of the run of missing entries entering the word
   off = align_up(off + sizeof(int) * (size_t)n3 * ((n2 + 31) / 32), 16);
+  L.tw = off;  // generic transform: the n3 twiddles exp(-2 pi i m / n3)
+  if (!specialised) off = align_up(off + sizeof(cx<T>) * (size_t)n3, 16);
   const size_t spec_bytes = specialised ? 0 : align_up(sizeof(cx<T>) * (size_t)S * n2, 16);
   const size_t spat_bytes = align_up(sizeof(T) * (size_t)n2 * slab_stride(n3), 16);
   L.slab_bytes = spec_bytes + spat_bytes;
@@ -298,56 +302,6 @@ __device__ __forceinline__ double dw_term(cx<T> rnew, cx<T> rold, cx<T> dz, int 
 }
 
 // ---------------------------------------------------------------------------
-// Generic (any n3) direct transforms of one tube: the sums of Eq. (bar BA-k)
-// and Eq. (barAAk).
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ void generic_irdft(const cx<T>* spec, int sstride, T* spat, int n3, const cx<T>* __restrict__ twg) {
-  const int S = n3 / 2 + 1;
-  const bool even = (n3 % 2) == 0;
-  const int kmax = even ? S - 2 : S - 1;  // slices with a conjugate partner
-  const T inv = T(1) / T(n3);
-  for (int l = 0; l < n3; ++l) {
-    T acc = spec[0].re;
-    int idx = l;  // k l mod n3, advanced by l per k
-    for (int k = 1; k <= kmax; ++k) {
-      const cx<T> w = twg[idx];
-      const cx<T> v = spec[k * sstride];
-      acc += T(2) * (v.re * w.re + v.im * w.im);  // 2 Re(v conj(w))
-      idx += l;
-      if (idx >= n3) idx -= n3;
-    }
-    if (even) acc += ((l & 1) ? -spec[(S - 1) * sstride].re : spec[(S - 1) * sstride].re);
-    spat[l] = acc * inv;
-  }
-}
-
-// Forward transform of a tube minus the spectrum zsub (R~ = W~ - Z~).  With
-// dz (Z~^{l+1} - Z~^l) non-null, dw2 accumulates the weighted |W~^{l+1} -
-// W~^l|^2 of the half spectrum (weight 2 for slices with a conjugate partner).
-template <typename T>
-__device__ void generic_rdft_sub(const T* spat, const cx<T>* __restrict__ zsub, cx<T>* out, size_t stride, int n3,
-                                 const cx<T>* __restrict__ twg, const cx<T>* __restrict__ dz, double& dw2) {
-  const int S = n3 / 2 + 1;
-  for (int k = 0; k < S; ++k) {
-    cx<T> acc = {T(0), T(0)};
-    int idx = 0;  // k l mod n3, advanced by k per l
-    for (int l = 0; l < n3; ++l) {
-      const cx<T> w = twg[idx];
-      const T x = spat[l];
-      acc.re += x * w.re;
-      acc.im += x * w.im;
-      idx += k;
-      if (idx >= n3) idx -= n3;
-    }
-    if (k == 0 || (2 * k == n3)) acc.im = T(0);
-    const cx<T> rn = zsub ? acc - zsub[k * stride] : acc;
-    if (dz) dw2 += dw_term(rn, out[k * stride], dz[k * stride], k, n3);
-    out[k * stride] = rn;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // MODE_ITER: phases A, B, C (init != 0: W = P_Omega(G), the initial point, in
 //            place of the W-step).
 // MODE_W   : W = iDFT(Z~ + R~); optional copy to Wout (column-major), partial
@@ -463,31 +417,64 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       }
     }
   } else {
-    for (int t = tid; t < n2; t += nt) {
-      for (int k = 0; k < S; ++k) {
-        const size_t o = (size_t)k * n2 + t;
-        cx<T> v;
-        if (MODE == MODE_ITER || MODE == MODE_GRAD) v = zrow[o];
-        else if (MODE == MODE_W) v = zrow[o] + rrow[o];
-        else v = rrow[o];
-        spec[k * n2 + t] = v;
-      }
+    // the half spectrum of the slab ([k][n2], as stored) and the twiddles
+    cx<T>* tw = reinterpret_cast<cx<T>*>(smem + lay.tw);
+    for (int m = tid; m < n3; m += nt) tw[m] = d.twg[m];
+    for (int e = tid; e < S * n2; e += nt) {
+      cx<T> v;
+      if (MODE == MODE_ITER || MODE == MODE_GRAD) v = zrow[e];
+      else if (MODE == MODE_W) v = zrow[e] + rrow[e];
+      else v = rrow[e];
+      spec[e] = v;
     }
     __syncthreads();
-    for (int t = tid; t < n2; t += nt) {
+    // Eq. (barAAk) for any n3, as a product of the spectrum with the DFT matrix:
+    // x_l = (1/n3) (X_0 + 2 sum_{k=1}^{kmax} Re(X_k conj(w_{kl})) [+ (-1)^l X_{n3/2}]),
+    // w_m = exp(-2 pi i m / n3), for items of one tube and kTL consecutive rows l,
+    // tube index fastest (a warp reads one slice of 32 tubes and shares the
+    // twiddles)
+    const bool even = (n3 % 2) == 0;
+    const int kmax = even ? S - 2 : S - 1;
+    const T inv = T(1) / T(n3);
+    const int nlb = (n3 + kTL - 1) / kTL;
+    for (int e = tid; e < nlb * n2; e += nt) {
+      const int lb = e / n2, t = e - lb * n2, l0 = lb * kTL;
+      T acc[kTL];
+      const T s0 = spec[t].re;
+#pragma unroll
+      for (int j = 0; j < kTL; ++j) acc[j] = s0;
+      int base = 0;  // k l0 mod n3
+      for (int k = 1; k <= kmax; ++k) {
+        base += l0;
+        if (base >= n3) base -= n3;
+        const cx<T> v = spec[(size_t)k * n2 + t];
+        int idx = base;  // k (l0 + j) mod n3
+#pragma unroll
+        for (int j = 0; j < kTL; ++j) {
+          const cx<T> w = tw[idx];
+          acc[j] += T(2) * (v.re * w.re + v.im * w.im);
+          idx += k;
+          if (idx >= n3) idx -= n3;
+        }
+      }
+      const T sn = even ? spec[(size_t)(S - 1) * n2 + t].re : T(0);
       T* col = spat + (size_t)t * LP;
-      generic_irdft<T>(spec + t, n2, col, n3, d.twg);
-      if (MODE == MODE_ITER) {
-        for (int l = 0; l < n3; ++l) {
+#pragma unroll
+      for (int j = 0; j < kTL; ++j) {
+        const int l = l0 + j;
+        if (l >= n3) break;
+        T a = acc[j];
+        if (even) a += (l & 1) ? -sn : sn;
+        T x = a * inv;
+        if (MODE == MODE_ITER) {
           const bool ob = (msk[l * mwords + (t >> 5)] >> (t & 31)) & 1u;
-          col[l] = ob ? __ldg(Gi + (size_t)l * n2 + t) : col[l] * zfac;
-        }
-      } else if (MODE == MODE_GRAD) {
-        for (int l = 0; l < n3; ++l) {
+          x = ob ? __ldg(Gi + (size_t)l * n2 + t) : x * zfac;
+        } else if (MODE == MODE_GRAD) {
           const bool ob = (msk[l * mwords + (t >> 5)] >> (t & 31)) & 1u;
-          col[l] = ob ? col[l] - __ldg(Gi + (size_t)l * n2 + t) : T(0);
-          gsum += (double)col[l] * (double)col[l];
+          x = ob ? x - __ldg(Gi + (size_t)l * n2 + t) : T(0);
+          gsum += (double)x * (double)x;
         }
+        col[l] = x;
       }
     }
   }
@@ -545,10 +532,46 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       }
     }
   } else {
-    for (int t = tid; t < n2; t += nt) {
+    // Eq. (bar BA-k) for any n3, as a product of the slab with the DFT matrix:
+    // X_k = sum_l x_l w_{kl} for k < S, for items of one tube and kTL consecutive
+    // slices k, tube index fastest
+    const cx<T>* tw = reinterpret_cast<const cx<T>*>(smem + lay.tw);
+    const int nkb = (S + kTL - 1) / kTL;
+    for (int e = tid; e < nkb * n2; e += nt) {
+      const int kb = e / n2, t = e - kb * n2, k0 = kb * kTL;
+      cx<T> acc[kTL];
+#pragma unroll
+      for (int j = 0; j < kTL; ++j) acc[j] = cx<T>{T(0), T(0)};
+      int idx[kTL], inc[kTL];  // (k0 + j) l mod n3, advanced by (k0 + j) mod n3 (< n3)
+#pragma unroll
+      for (int j = 0; j < kTL; ++j) {
+        idx[j] = 0;
+        inc[j] = (k0 + j) % n3;
+      }
+      const T* col = spat + (size_t)t * LP;
+      for (int l = 0; l < n3; ++l) {
+        const T x = col[l];
+#pragma unroll
+        for (int j = 0; j < kTL; ++j) {
+          const cx<T> w = tw[idx[j]];
+          acc[j].re += x * w.re;
+          acc[j].im += x * w.im;
+          idx[j] += inc[j];
+          if (idx[j] >= n3) idx[j] -= n3;
+        }
+      }
       const size_t o = (size_t)i1 * S * n2 + t;
-      generic_rdft_sub<T>(spat + (size_t)t * LP, (MODE == MODE_GRAD) ? nullptr : zrow + t, d.Rt + o, (size_t)n2,
-                          n3, d.twg, track ? d.dZt + o : nullptr, dw2);
+#pragma unroll
+      for (int j = 0; j < kTL; ++j) {
+        const int k = k0 + j;
+        if (k >= S) break;
+        cx<T> a = acc[j];
+        if (k == 0 || (2 * k == n3)) a.im = T(0);
+        const size_t ok = o + (size_t)k * n2;
+        const cx<T> rn = (MODE == MODE_GRAD) ? a : a - zrow[(size_t)k * n2 + t];
+        if (track) dw2 += dw_term(rn, d.Rt[ok], d.dZt[ok], k, n3);
+        d.Rt[ok] = rn;
+      }
     }
   }
   if (track) {
