@@ -641,9 +641,17 @@ def batched_form(torch, dev, stream, flush, steps, warmup):
         cs = contexts(mixed)
         with tc.Batch(cs, stream=sptr) as B:
             B.iterate(2 * 4)  # tuning trials (two per candidate branch count), real iterations
+            n0, _ = B.launches()
             ms = _timed(torch, stream, flush, lambda: B.iterate(iters), steps, warmup)
+            n1, loop = B.launches()
             res[f"batch_{label}"] = BATCH * iters * steps / (ms / 1e3)
             res[f"branches_{label}"] = B.branches()
+            res[f"graph_launches_per_call_{label}"] = (n1 - n0) / (steps + warmup)
+            res[f"device_loop_{label}"] = loop
+        tiles = {}
+        for c in cs:
+            tiles[str(c.tile())] = tiles.get(str(c.tile()), 0) + 1
+        res[f"transform_tiles_{label}"] = tiles
         ms = _timed(torch, stream, flush, lambda: [c.iterate(iters, count=False) for c in cs], steps, warmup)
         res[f"sequential_{label}"] = BATCH * iters * steps / (ms / 1e3)
         for q in NMSE_SAMPLE:

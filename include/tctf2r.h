@@ -211,6 +211,16 @@ typedef struct tc_batch tc_batch;
 tc_status tc_batch_create(tc_batch** out, tc_ctx* const* ctxs, int32_t count, void* cuda_stream);
 tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters);
 tc_status tc_batch_branches(tc_batch* b, int32_t* branches);
+/* Once the tuning trials have chosen K, tc_batch_iterate runs all of its
+ * remaining iterations in ONE graph launch: a CUDA while-node whose body is the
+ * batched iteration followed by a one-thread kernel that counts the iterations
+ * down on the device (the count only decreases, so the loop ends after n
+ * passes).  Where conditional graph nodes are unavailable it falls back to one
+ * launch per iteration.
+ * tc_batch_launches: launches receives the graph launches made by
+ *   tc_batch_iterate so far; device_loop (may be NULL) receives 1 once the
+ *   device-side loop is in use.  Errors: TC_ERR_ARG. */
+tc_status tc_batch_launches(tc_batch* b, int64_t* launches, int32_t* device_loop);
 tc_status tc_batch_free(tc_batch* b);
 
 /* Differentiation form: the factor terms of f0 (Eq. (TETP-optim)) with W held
@@ -268,6 +278,17 @@ tc_status tc_grad_free(tc_grad* g);
  * TC_ERR_NUMERIC. */
 tc_status tc_complete_static(const tc_params* p, const void* G, const uint8_t* mask, const void* Y0,
                              const void* X0, int32_t n_iters, void* W, double* f0, void* cuda_stream);
+
+/* Tile of the mode-3 transform chosen for this context (the library's own
+ * tuning, no counterpart in the paper).  Tube lengths other than the ones with
+ * dedicated kernels (7, 112, 168 in FP32; 7 in FP64) use a transform written as
+ * a product with the DFT matrix of Eq. (bar BA-k) / Eq. (barAAk), each work
+ * item covering one tube and slab_tile rows (inverse) or slices (forward);
+ * tc_init times slab_tile = 2, 4 and 8 on the initial pass (every choice gives
+ * the same sums in the same order) and keeps the fastest.
+ *   slab_tile : receives the chosen tile, 0 for a dedicated-kernel length.
+ * Errors: TC_ERR_ARG. */
+tc_status tc_tile(tc_ctx* c, int32_t* slab_tile);
 
 /* Release a context and its device memory.  NULL-safe.  Synchronises the
  * context's stream first. */

@@ -19,7 +19,8 @@ enum SlabMode : int { MODE_ITER = 0, MODE_W = 1, MODE_R = 2, MODE_GRAD = 3 };
 // on one scheduler and cap a thread at 168 registers); tubes beyond the thread
 // count loop.
 __host__ __device__ constexpr int slab_max_threads(int) { return 256; }
-// Rows (inverse) or slices (forward) per item of the generic transform.
+// Rows (inverse) or slices (forward) per item of the generic transform, by
+// default; the engine picks among 2, 4 and 8 by timing (slab_tile_candidates).
 constexpr int kTL = 4;
 
 // Odd stride between tubes in the slab (n3 values per tube).
@@ -310,7 +311,9 @@ __device__ __forceinline__ double dw_term(cx<T> rnew, cx<T> rold, cx<T> dz, int 
 // Layouts used here: G row-major [i1][n3][n2] and mask words row-major
 // [i1][n3][ceil(n2/32)] (written by k_pack), copied to shared memory.
 // ---------------------------------------------------------------------------
-template <typename T, int L, int MODE>
+// TL: rows (inverse) or slices (forward) per item of the generic transform
+// (L = 0); every TL gives the same sums in the same order.
+template <typename T, int L, int MODE, int TL = kTL>
 __global__ void __launch_bounds__(slab_max_threads(L), 1)
     k_slab(Dev<T> d, T* __restrict__ Wout, int slabs_in_smem, int init) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -430,19 +433,19 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
     __syncthreads();
     // Eq. (barAAk) for any n3, as a product of the spectrum with the DFT matrix:
     // x_l = (1/n3) (X_0 + 2 sum_{k=1}^{kmax} Re(X_k conj(w_{kl})) [+ (-1)^l X_{n3/2}]),
-    // w_m = exp(-2 pi i m / n3), for items of one tube and kTL consecutive rows l,
+    // w_m = exp(-2 pi i m / n3), for items of one tube and TL consecutive rows l,
     // tube index fastest (a warp reads one slice of 32 tubes and shares the
     // twiddles)
     const bool even = (n3 % 2) == 0;
     const int kmax = even ? S - 2 : S - 1;
     const T inv = T(1) / T(n3);
-    const int nlb = (n3 + kTL - 1) / kTL;
+    const int nlb = (n3 + TL - 1) / TL;
     for (int e = tid; e < nlb * n2; e += nt) {
-      const int lb = e / n2, t = e - lb * n2, l0 = lb * kTL;
-      T acc[kTL];
+      const int lb = e / n2, t = e - lb * n2, l0 = lb * TL;
+      T acc[TL];
       const T s0 = spec[t].re;
 #pragma unroll
-      for (int j = 0; j < kTL; ++j) acc[j] = s0;
+      for (int j = 0; j < TL; ++j) acc[j] = s0;
       int base = 0;  // k l0 mod n3
       for (int k = 1; k <= kmax; ++k) {
         base += l0;
@@ -450,7 +453,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
         const cx<T> v = spec[(size_t)k * n2 + t];
         int idx = base;  // k (l0 + j) mod n3
 #pragma unroll
-        for (int j = 0; j < kTL; ++j) {
+        for (int j = 0; j < TL; ++j) {
           const cx<T> w = tw[idx];
           acc[j] += T(2) * (v.re * w.re + v.im * w.im);
           idx += k;
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       const T sn = even ? spec[(size_t)(S - 1) * n2 + t].re : T(0);
       T* col = spat + (size_t)t * LP;
 #pragma unroll
-      for (int j = 0; j < kTL; ++j) {
+      for (int j = 0; j < TL; ++j) {
         const int l = l0 + j;
         if (l >= n3) break;
         T a = acc[j];
@@ -533,18 +536,18 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
     }
   } else {
     // Eq. (bar BA-k) for any n3, as a product of the slab with the DFT matrix:
-    // X_k = sum_l x_l w_{kl} for k < S, for items of one tube and kTL consecutive
+    // X_k = sum_l x_l w_{kl} for k < S, for items of one tube and TL consecutive
     // slices k, tube index fastest
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(smem + lay.tw);
-    const int nkb = (S + kTL - 1) / kTL;
+    const int nkb = (S + TL - 1) / TL;
     for (int e = tid; e < nkb * n2; e += nt) {
-      const int kb = e / n2, t = e - kb * n2, k0 = kb * kTL;
-      cx<T> acc[kTL];
+      const int kb = e / n2, t = e - kb * n2, k0 = kb * TL;
+      cx<T> acc[TL];
 #pragma unroll
-      for (int j = 0; j < kTL; ++j) acc[j] = cx<T>{T(0), T(0)};
-      int idx[kTL], inc[kTL];  // (k0 + j) l mod n3, advanced by (k0 + j) mod n3 (< n3)
+      for (int j = 0; j < TL; ++j) acc[j] = cx<T>{T(0), T(0)};
+      int idx[TL], inc[TL];  // (k0 + j) l mod n3, advanced by (k0 + j) mod n3 (< n3)
 #pragma unroll
-      for (int j = 0; j < kTL; ++j) {
+      for (int j = 0; j < TL; ++j) {
         idx[j] = 0;
         inc[j] = (k0 + j) % n3;
       }
@@ -552,7 +555,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       for (int l = 0; l < n3; ++l) {
         const T x = col[l];
 #pragma unroll
-        for (int j = 0; j < kTL; ++j) {
+        for (int j = 0; j < TL; ++j) {
           const cx<T> w = tw[idx[j]];
           acc[j].re += x * w.re;
           acc[j].im += x * w.im;
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(slab_max_threads(L), 1)
       }
       const size_t o = (size_t)i1 * S * n2 + t;
 #pragma unroll
-      for (int j = 0; j < kTL; ++j) {
+      for (int j = 0; j < TL; ++j) {
         const int k = k0 + j;
         if (k >= S) break;
         cx<T> a = acc[j];

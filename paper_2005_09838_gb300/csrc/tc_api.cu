@@ -210,11 +210,19 @@ struct tc_batch {
   std::vector<float> best_ms;         // best trial time per candidate
   std::vector<int> trials;
   int chosen = -1;
+  cudaGraphExec_t loop = nullptr;     // after tuning: n iterations in one launch (device-side loop)
+  bool loop_failed = false;           // conditional nodes unavailable: one launch per iteration
+  unsigned int* left = nullptr;       // device counter of the iterations still to run
+  long long launches = 0;             // graph launches made by tc_batch_iterate
   std::vector<cudaGraph_t> child;     // one captured iteration per instance
   std::vector<cudaEvent_t> ctx_ev;
   cudaEvent_t t0 = nullptr, t1 = nullptr, done = nullptr;
 
   void release() {
+    if (loop) cudaGraphExecDestroy(loop);
+    loop = nullptr;
+    if (left) cudaFree(left);
+    left = nullptr;
     for (auto e : exec)
       if (e) cudaGraphExecDestroy(e);
     for (auto g : child)
@@ -251,6 +259,69 @@ tc_status batch_build(tc_batch* b, int K, cudaGraphExec_t* out, std::string& err
   if (e != cudaSuccess) {
     cudaGetLastError();
     err = std::string("batched graph build failed: ") + cudaGetErrorString(e);
+    return TC_ERR_CUDA;
+  }
+  return TC_OK;
+}
+
+// Device-side loop of the batched completion: before the launch the counter
+// holds n >= 1; each pass of the while body runs one iteration of every
+// instance and then this one-thread kernel, which counts down and keeps the
+// loop going while iterations remain (the count only decreases, so the loop
+// ends after n passes).
+__global__ void k_batch_set(unsigned int* left, unsigned int n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *left = n;
+}
+__global__ void k_batch_count(unsigned int* left, cudaGraphConditionalHandle h) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned int n = *left;
+    const unsigned int rest = n > 1u ? n - 1u : 0u;
+    *left = rest;
+    cudaGraphSetConditional(h, rest > 0u ? 1u : 0u);
+  }
+}
+
+// The loop graph: a while node whose body is the batched iteration with K
+// chains (as batch_build) followed by k_batch_count.
+tc_status batch_build_loop(tc_batch* b, int K, cudaGraphExec_t* out, std::string& err) {
+  cudaGraph_t parent = nullptr;
+  cudaError_t e = cudaGraphCreate(&parent, 0);
+  cudaGraphConditionalHandle h{};
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, parent, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, parent, nullptr, nullptr, 0, &cp);
+  cudaGraph_t body = (e == cudaSuccess) ? cp.conditional.phGraph_out[0] : nullptr;
+  std::vector<cudaGraphNode_t> last(K, nullptr);
+  for (size_t i = 0; i < b->ctxs.size() && e == cudaSuccess; ++i) {
+    const int j = (int)(i % K);
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddChildGraphNode(&node, body, last[j] ? &last[j] : nullptr, last[j] ? 1 : 0, b->child[i]);
+    last[j] = node;
+  }
+  std::vector<cudaGraphNode_t> tails;
+  for (auto n : last)
+    if (n) tails.push_back(n);
+  if (e == cudaSuccess) {
+    cudaKernelNodeParams kp{};
+    void* args[] = {&b->left, &h};
+    kp.func = (void*)k_batch_count;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    cudaGraphNode_t knode = nullptr;
+    e = cudaGraphAddKernelNode(&knode, body, tails.data(), tails.size(), &kp);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, parent, 0);
+  if (parent) cudaGraphDestroy(parent);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    err = std::string("device-side loop of the batch not available: ") + cudaGetErrorString(e);
     return TC_ERR_CUDA;
   }
   return TC_OK;
@@ -312,6 +383,12 @@ tc_status tc_batch_create(tc_batch** out, tc_ctx* const* ctxs, int32_t count, vo
   b->best_ms.assign(b->cand.size(), 1e30f);
   b->trials.assign(b->cand.size(), 0);
   if (b->cand.size() == 1) b->chosen = 0;
+  if (cudaMalloc(&b->left, sizeof(unsigned int)) != cudaSuccess) {
+    cudaGetLastError();
+    b->release();
+    delete b;
+    return fail(TC_ERR_NOMEM, "allocation of the batch counter failed");
+  }
   *out = b;
   return TC_OK;
 }
@@ -331,6 +408,18 @@ tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ctx_ev[i], 0);
   }
   for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
+    if (b->chosen >= 0 && !b->loop && !b->loop_failed) {
+      std::string lerr;
+      b->loop_failed = batch_build_loop(b, b->cand[b->chosen], &b->loop, lerr) != TC_OK;
+    }
+    if (b->chosen >= 0 && b->loop) {
+      // the remaining iterations in one launch: the loop runs on the device
+      k_batch_set<<<1, 32, 0, b->stream>>>(b->left, (unsigned int)(n_iters - it));
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaGraphLaunch(b->loop, b->stream);
+      ++b->launches;
+      break;
+    }
     if (b->chosen < 0) {
       // tuning: the candidate with the fewest trials, timed on its own
       size_t c = 0;
@@ -338,6 +427,7 @@ tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters) {
         if (b->trials[q] < b->trials[c]) c = q;
       e = cudaEventRecord(b->t0, b->stream);
       if (e == cudaSuccess) e = cudaGraphLaunch(b->exec[c], b->stream);
+      ++b->launches;
       if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(b->t1);
       float ms = 0.f;
@@ -349,6 +439,7 @@ tc_status tc_batch_iterate(tc_batch* b, int32_t n_iters) {
         b->chosen = (int)(std::min_element(b->best_ms.begin(), b->best_ms.end()) - b->best_ms.begin());
     } else {
       e = cudaGraphLaunch(b->exec[b->chosen], b->stream);
+      ++b->launches;
     }
   }
   // every context's later calls come after the batch
@@ -364,6 +455,21 @@ tc_status tc_batch_branches(tc_batch* b, int32_t* branches) {
   g_last_error.clear();
   if (!b || !branches) return fail(TC_ERR_ARG, "batch and branches are required");
   *branches = (b->chosen < 0) ? 0 : b->cand[b->chosen];
+  return TC_OK;
+}
+
+tc_status tc_batch_launches(tc_batch* b, int64_t* launches, int32_t* device_loop) {
+  g_last_error.clear();
+  if (!b || !launches) return fail(TC_ERR_ARG, "batch and launches are required");
+  *launches = b->launches;
+  if (device_loop) *device_loop = b->loop ? 1 : 0;
+  return TC_OK;
+}
+
+tc_status tc_tile(tc_ctx* c, int32_t* slab_tile) {
+  g_last_error.clear();
+  if (!c || !slab_tile) return fail(TC_ERR_ARG, "ctx and slab_tile are required");
+  *slab_tile = c->eng->slab_tile();
   return TC_OK;
 }
 

@@ -37,6 +37,14 @@ inline void slab_table(SlabFn<T> f[3]) {
   f[MODE_R] = k_slab<T, L, MODE_R>;
 }
 
+// Generic-length slab kernels with TL rows / slices per transform item.
+template <typename T, int TL>
+inline void slab_table_tl(SlabFn<T> f[3]) {
+  f[MODE_ITER] = k_slab<T, 0, MODE_ITER, TL>;
+  f[MODE_W] = k_slab<T, 0, MODE_W, TL>;
+  f[MODE_R] = k_slab<T, 0, MODE_R, TL>;
+}
+
 template <typename T, int L, int N1, int N2>
 inline void slab_f_table(SlabFn<T> f[3]) {
   f[MODE_ITER] = k_slab_f<T, L, N1, N2, MODE_ITER>;
@@ -458,6 +466,13 @@ class Engine final : public EngineBase {
     k_synth_init<T><<<fgrid, 256, 0, stream_>>>(d_);                    // Z~0 = X~0 Y~0
     k_gram_tiles<T><<<dim3(S_, ytiles), 256, 0, stream_>>>(d_);         // A of the first X-step
     if (xsplit_ || apre_) xa_fn_<<<S_, xa_threads_, xa_smem_, stream_>>>(d_);  // its A^+
+    if (!specialised_) {
+      // tile of the generic transform for this shape: each candidate runs the
+      // initial slab pass (it only depends on G and Z~0, so every run writes the
+      // same R~0), timed twice; the fastest is kept
+      tc_status st = tune_slab_tile(err);
+      if (st != TC_OK) return st;
+    }
     launch_slab(MODE_ITER, nullptr, 1, stream_);  // R~0 = DFT3(P_Omega(G) - Z0)
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(stream_);
@@ -718,6 +733,7 @@ class Engine final : public EngineBase {
     return TC_OK;
   }
 
+  int slab_tile() const override { return slab_tile_; }
   cudaStream_t stream() const override { return stream_; }
   bool poisoned() const override { return poisoned_; }
 
@@ -773,6 +789,49 @@ class Engine final : public EngineBase {
     }
     allocs_.push_back(q);
     return static_cast<U*>(q);
+  }
+
+  tc_status tune_slab_tile(std::string& err) {
+    const int cand[3] = {2, 4, 8};
+    SlabFn<T> tab[3][3];
+    slab_table_tl<T, 2>(tab[0]);
+    slab_table_tl<T, 4>(tab[1]);
+    slab_table_tl<T, 8>(tab[2]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TC_CUDA_TRY(cudaEventCreate(&e0));
+    TC_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 1;
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
+      for (int m = 0; m < 3 && e == cudaSuccess; ++m) e = allow_dynamic_smem((const void*)tab[c][m], slab_smem_);
+      for (int m = 0; m < 3; ++m) slab_[m] = tab[c][m];
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(e0, stream_);
+        if (e == cudaSuccess) launch_slab(MODE_ITER, nullptr, 1, stream_);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, stream_);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+      err = std::string("tuning of the generic slab kernel failed: ") + cudaGetErrorString(e);
+      poisoned_ = true;
+      return TC_ERR_CUDA;
+    }
+    for (int m = 0; m < 3; ++m) slab_[m] = tab[pick][m];
+    slab_tile_ = cand[pick];
+    return TC_OK;
   }
 
   void launch_slab(int mode, T* Wout, int init, cudaStream_t s) {
@@ -878,6 +937,7 @@ class Engine final : public EngineBase {
   bool mixed_ = false;
   bool xsplit_ = false;  // X-step as four kernels
   bool apre_ = false;    // one-CTA X-step with A^+ from k_xa on a graph branch
+  int slab_tile_ = 0;    // rows / slices per item of the generic transform (0: specialised length)
   int* rk_ = nullptr;    // step 5: slice ranks, counters and work (allocated when the rule is first on)
   int* rcnt_ = nullptr;
   cx<T>* rscr_ = nullptr;

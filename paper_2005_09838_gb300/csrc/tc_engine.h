@@ -23,6 +23,8 @@ struct EngineBase {
   // step 5 (rank vector): tol = 0 turns the rule off; ranks gets n3 values
   virtual tc_status set_rank_rule(double tol, int patience, std::string& err) = 0;
   virtual tc_status ranks(int* out, std::string& err) = 0;
+  // tile of the generic-length transform chosen at init (0: specialised length)
+  virtual int slab_tile() const = 0;
   virtual void release() = 0;
   // one iteration captured as a graph (the caller owns and destroys it)
   virtual tc_status capture_iteration(cudaGraph_t* out, std::string& err) = 0;

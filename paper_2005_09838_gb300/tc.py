@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_ARG", 2: "TC_ERR_NOMEM", 3: "TC_ERR_CUDA"
 
 # Entry points declared in include/tctf2r.h (checked by the tests).
 EXPORTS = ("tc_init", "tc_iterate", "tc_objective", "tc_result", "tc_profile", "tc_free", "tc_last_error",
-           "tc_version", "tc_rank_rule", "tc_ranks")
+           "tc_version", "tc_rank_rule", "tc_ranks", "tc_tile", "tc_batch_launches")
 
 
 class tc_params(ctypes.Structure):
@@ -95,6 +95,10 @@ def load(path: str | None = None):
     lib.tc_batch_iterate.restype = ctypes.c_int
     lib.tc_batch_branches.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.tc_batch_branches.restype = ctypes.c_int
+    lib.tc_batch_launches.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+    lib.tc_batch_launches.restype = ctypes.c_int
+    lib.tc_tile.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.tc_tile.restype = ctypes.c_int
     lib.tc_batch_free.argtypes = [P]
     lib.tc_batch_free.restype = ctypes.c_int
     lib.tc_free.argtypes = [P]
@@ -174,6 +178,13 @@ class Completion:
         consecutive iterations; tol = 0 turns it off."""
         _check(self._lib.tc_rank_rule(self._ctx, float(tol), int(patience)))
 
+    def tile(self) -> int:
+        """Tile of the generic-length transform chosen at init (tc_tile; 0 for a
+        dedicated-kernel length)."""
+        t = ctypes.c_int32(0)
+        _check(self._lib.tc_tile(self._ctx, ctypes.byref(t)))
+        return t.value
+
     def ranks(self):
         """The rank of every frontal slice (n3 values, tc_ranks)."""
         out = (ctypes.c_int32 * int(self.params.n3))()
@@ -241,6 +252,14 @@ class Batch:
         k = ctypes.c_int32(0)
         _check(self._lib.tc_batch_branches(self._b, ctypes.byref(k)))
         return k.value
+
+    def launches(self):
+        """(graph launches made by iterate so far, 1 once the device-side loop runs
+        whole calls in one launch)."""
+        n = ctypes.c_int64(0)
+        loop = ctypes.c_int32(0)
+        _check(self._lib.tc_batch_launches(self._b, ctypes.byref(n), ctypes.byref(loop)))
+        return n.value, loop.value
 
     def close(self):
         if self._b:

@@ -62,17 +62,27 @@ def test_batched_instances_match_their_solo_runs():
         assert B.branches() == 0
         B.iterate(5)
         assert B.branches() in (1, 4, len(CASES))
-        B.iterate(2)          # the chosen graph
+        n0, loop = B.launches()
+        assert loop == 1      # after the trials, the device-side loop
+        B.iterate(2)          # the chosen graph: two iterations in one launch
+        B.iterate(7)
+        n1, _ = B.launches()
+        assert n1 - n0 == 2
     for c in solo:
-        c.iterate(10)
+        c.iterate(17)
     for (prec, shape, r, obs), a, b in zip(CASES, batched, solo):
         Wa, _, _ = a.result_numpy()
         Wb, _, _ = b.result_numpy()
         assert np.array_equal(Wa, Wb), (prec, shape)
         assert a.objective()[0] == b.objective()[0]
+    # the transform tile chosen at init: 2, 4 or 8 for generic lengths, 0 where a
+    # dedicated kernel exists (7, 112, 168 in FP32; 7 in FP64)
+    for (prec, shape, r, obs), a in zip(CASES, batched):
+        dedicated = shape[2] == 7 or (prec != "fp64" and shape[2] in (112, 168))
+        assert (a.tile() == 0) if dedicated else (a.tile() in (2, 4, 8)), (prec, shape, a.tile())
     # and the oracle agrees with one of them
     prec, shape, r, _ = CASES[0]
-    ref = O.tctf2r(insts[0]["G"], insts[0]["mask"], r, *SETTING, insts[0]["Y0"], iters=10)
+    ref = O.tctf2r(insts[0]["G"], insts[0]["mask"], r, *SETTING, insts[0]["Y0"], iters=17)
     W0, _, _ = batched[0].result_numpy()
     W0 = wl.from_colmajor(W0, shape)
     assert np.linalg.norm(W0 - ref["W"]) <= 1e-10 * np.linalg.norm(ref["W"])
