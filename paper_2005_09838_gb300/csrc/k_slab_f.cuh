@@ -32,6 +32,8 @@
 namespace tc {
 
 constexpr int kSlabFThreads = 512;
+// Items per thread whose global loads are issued together in the first split phase.
+constexpr int kSlabFBatch = 4;
 
 // Floats between consecutive tubes: room for the M + 1 complex values of the
 // half spectrum, even (complex slots are 8-byte aligned) with an odd number of
@@ -148,36 +150,45 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
     for (int j = tid; j < 6 * n2; j += nt) wtab[j] = d.winv[j];
 
   // ---- A1: half spectrum -> packed sequence z (pairs k, M - k) -----------------------
-  if (MODE != MODE_W) {
-    // the half spectrum lands in slots 0..M of every tube through asynchronous
-    // copies (all in flight at once), then is split in place
-    const cx<T>* src = (MODE == MODE_ITER || MODE == MODE_GRAD) ? zrow : rrow;
-    ItemIter it(tid, n2);
-    for (int e = tid; e < (M + 1) * n2; e += nt, it.advance(nt, n2))
-      cp_async_elem(reinterpret_cast<cx<T>*>(buf + (size_t)it.t * LP) + it.g, src + e);
-    cp_async_wait_all();
-    __syncthreads();
-  }
+  // Each item reads the pair (k, M - k) of one tube straight from the stored
+  // half spectrum (coalesced along the tubes), kSlabFBatch items per thread with all
+  // their loads in flight, and writes the split values to the tube's slots.
   {
-    ItemIter it(tid, n2);
-    for (int e = tid; e < (M / 2 + 1) * n2; e += nt, it.advance(nt, n2)) {
-      const int k = it.g, t = it.t;
-      const int kc = M - k;
-      T* tb = buf + (size_t)t * LP;
-      cx<T> a, b;
-      if (MODE == MODE_W) {
-        a = ldg_cx(zrow + (size_t)k * n2 + t) + ldg_cx(rrow + (size_t)k * n2 + t);
-        b = ldg_cx(zrow + (size_t)kc * n2 + t) + ldg_cx(rrow + (size_t)kc * n2 + t);
-      } else {
-        a = ld_slot(tb, k);
-        b = ld_slot(tb, kc);
+    constexpr int U = kSlabFBatch;
+    const int nitem = (M / 2 + 1) * n2;
+    const cx<T>* src = (MODE == MODE_R) ? rrow : zrow;
+    for (int e0 = tid; e0 < nitem; e0 += U * nt) {
+      cx<T> a[U], b[U];
+      int kk[U], tt[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nt;
+        kk[u] = e / n2;
+        tt[u] = e - kk[u] * n2;
+        if (e < nitem) {
+          const size_t ok = (size_t)kk[u] * n2 + tt[u], oc = (size_t)(M - kk[u]) * n2 + tt[u];
+          if (MODE == MODE_W) {
+            a[u] = ldg_cx(zrow + ok) + ldg_cx(rrow + ok);
+            b[u] = ldg_cx(zrow + oc) + ldg_cx(rrow + oc);
+          } else {
+            a[u] = ldg_cx(src + ok);
+            b[u] = ldg_cx(src + oc);
+          }
+        }
       }
-      if (k == 0) {  // DC and Nyquist slices are real
-        a.im = T(0);
-        b.im = T(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (e0 + u * nt >= nitem) break;
+        const int k = kk[u], kc = M - k;
+        T* tb = buf + (size_t)tt[u] * LP;
+        cx<T> av = a[u], bv = b[u];
+        if (k == 0) {  // DC and Nyquist slices are real
+          av.im = T(0);
+          bv.im = T(0);
+        }
+        st_slot(tb, k, inv_split<T, L>(av, bv, k));
+        if (k != 0 && k != kc) st_slot(tb, kc, inv_split<T, L>(bv, av, kc));
       }
-      st_slot(tb, k, inv_split<T, L>(a, b, k));
-      if (k != 0 && k != kc) st_slot(tb, kc, inv_split<T, L>(b, a, kc));
     }
   }
   __syncthreads();
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(kSlabFThreads, 1) k_slab_f(Dev<T> d, T* __rest
     return;
   }
 
-  // ---- W-step (one thread per row) ---------------------------------------------------------
+  // ---- W-step (rows split into segments of mask words) ---------------------------------------
   if (wsolve) {
     // rows split into nseg segments so that every thread has one (row, segment)
     const int nseg = max(1, nt / L);

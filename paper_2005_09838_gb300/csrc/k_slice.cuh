@@ -946,7 +946,8 @@ __device__ __forceinline__ cx<double>* real_gram_Dg(cx<double>* M, int rr) { ret
 static __device__ __noinline__ int real_gj_fp64(const double* a, double* work, double* piv, int r) {
   const int t = threadIdx.x, nt = blockDim.x, rr = r * r;
   for (int e = t; e < rr; e += nt) work[e] = a[e];
-  if (t == 0) piv[0] = (a[0] > 0.0 && isfinite(a[0])) ? 1.0 / a[0] : 0.0;
+  // pivot reciprocals: FP32 seed and two Newton steps (an FP64 division is slow here)
+  if (t == 0) piv[0] = (a[0] > 0.0 && isfinite(a[0])) ? rcp_refined(a[0]) : 0.0;
   __syncthreads();
   for (int p = 0; p < r; ++p) {
     const double* src = work + (p & 1) * rr;
@@ -960,7 +961,7 @@ static __device__ __noinline__ int real_gj_fp64(const double* a, double* work, d
       else if (j == p) v = -src[i * r + p] * ip;
       else v = fma(-src[i * r + p], src[p * r + j] * ip, src[e]);
       dst[e] = v;
-      if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = (v > 0.0 && isfinite(v)) ? 1.0 / v : 0.0;
+      if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = (v > 0.0 && isfinite(v)) ? rcp_refined(v) : 0.0;
     }
     __syncthreads();
   }
@@ -1009,7 +1010,8 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
     }
     an = warp_sum(an);
     in = warp_sum(in);
-    if (tid == 0) sred[1] = (ok && isfinite(in) && sqrt(an) * sqrt(in) < 0.5 / rtol) ? 1.0 : 0.0;
+    // ||G||_F ||G^-1||_F < 1/(2 rtol), compared squared
+    if (tid == 0) sred[1] = (ok && isfinite(in) && an * in < 0.25 / (rtol * rtol)) ? 1.0 : 0.0;
   }
   __syncthreads();
   if (sred[1] != 0.0) {
