@@ -149,7 +149,9 @@ tc_status tc_result(tc_ctx* c, void* W, void* X, void* Y, int32_t dst_on_device)
  *        the four kernels of one iteration, in launch order: the X-step
  *        contraction R~Y~^H, the X-step (with the r x r Y-step preparation),
  *        the Y-step, and the slab kernel (synthesis / inverse DFT / W-step /
- *        forward DFT).
+ *        forward DFT).  The pseudo-inverse A^+ of the next X-step, which the
+ *        captured iteration forms on a graph branch beside the slab kernel, runs
+ *        after the slab kernel here and is not timed.
  * Errors: TC_ERR_ARG (n_iters < 1 or ms NULL), TC_ERR_CUDA, TC_ERR_STATE. */
 tc_status tc_profile(tc_ctx* c, int32_t n_iters, double* ms);
 

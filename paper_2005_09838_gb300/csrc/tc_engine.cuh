@@ -753,10 +753,12 @@ class Engine final : public EngineBase {
       cudaEventRecord(ev[1], stream_);
       launch_xstep(stream_);
       cudaEventRecord(ev[2], stream_);
-      launch_ystep(stream_);  // with A^+ of the next X-step (four-kernel form)
+      launch_ystep(stream_, nullptr, false);  // A^+ of the next X-step is formed below, untimed
       cudaEventRecord(ev[3], stream_);
       launch_slab(MODE_ITER, nullptr, 0, stream_);
       cudaEventRecord(ev[4], stream_);
+      // in the captured iteration k_xa runs beside the slab kernel; here after it
+      if (xsplit_ || apre_) xa_fn_<<<S_, xa_threads_, xa_smem_, stream_>>>(d_);
       if (d_.rk) launch_rank(stream_);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
@@ -854,13 +856,13 @@ class Engine final : public EngineBase {
   // Grams.  With a branch stream (graph capture) A^+ is formed there, beside
   // the rest of the iteration; the return value says whether it was, and the
   // caller then joins on ev_join_.  Without one it follows on s.
-  bool launch_ystep(cudaStream_t s, cudaStream_t branch = nullptr) {
+  bool launch_ystep(cudaStream_t s, cudaStream_t branch = nullptr, bool with_xa = true) {
     const int tw = 32 * ystep_cpl(rp_);
     dim3 g(S_, (n2_ + tw - 1) / tw);
     if (tcy_) tck_.dcon<<<dim3(S_, (n2_ + 127) / 128, ksplit_), 256, tck_.dsm, s>>>(d_);
     ystep_<<<g, kYThreads, ystep_smem_, s>>>(d_);
     bool forked = false;
-    if (xsplit_ || apre_) {
+    if ((xsplit_ || apre_) && with_xa) {
       if (branch && cudaEventRecord(ev_fork_, s) == cudaSuccess &&
           cudaStreamWaitEvent(branch, ev_fork_, 0) == cudaSuccess) {
         xa_fn_<<<S_, xa_threads_, xa_smem_, branch>>>(d_);
