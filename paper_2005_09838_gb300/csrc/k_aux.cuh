@@ -30,68 +30,109 @@ __global__ void k_pack(const T* __restrict__ Gin, const uint8_t* __restrict__ Mi
 // real factor along mode 3, written to the half spectrum [S][r][n]:
 //   transposed = 0: input n x r x n3 (X0: i fastest, then s)
 //   transposed = 1: input r x n x n3 (Y0: s fastest, then i)
-// twg[m] = exp(-2 pi i m / n3); four interleaved partial sums.
+// twg[m] = exp(-2 pi i m / n3).  Each work item is one tube (s, i) and kFT
+// consecutive slices k, so every input value read feeds kFT outputs; the
+// items run along the input's fastest index (coalesced loads).
+constexpr int kFT = 4;
+
+__device__ __forceinline__ void factor_item(size_t e, int n, int r, int transposed, int& i, int& s, size_t& blk) {
+  if (transposed) {
+    s = (int)(e % r);
+    i = (int)((e / r) % n);
+    blk = e / ((size_t)r * n);
+  } else {
+    i = (int)(e % n);
+    s = (int)((e / n) % r);
+    blk = e / ((size_t)n * r);
+  }
+}
+
 template <typename T>
 __global__ void k_factor_dft(const T* __restrict__ in, cx<T>* __restrict__ out, int n, int r, int n3, int transposed,
                              const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
-  const size_t total = (size_t)S * r * n;
+  const size_t total = (size_t)((S + kFT - 1) / kFT) * r * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % n);
-    const int s = (int)((e / n) % r);
-    const int k = (int)(e / ((size_t)n * r));
-    cx<T> acc[4] = {};
-    int m = 0;  // k * l mod n3
+    int i, s;
+    size_t blk;
+    factor_item(e, n, r, transposed, i, s, blk);
+    const int k0 = (int)blk * kFT;
+    cx<T> acc[kFT];
+    int m[kFT], inc[kFT];  // (k0 + j) l mod n3, advanced by (k0 + j) mod n3
+#pragma unroll
+    for (int j = 0; j < kFT; ++j) {
+      acc[j] = cx<T>{T(0), T(0)};
+      m[j] = 0;
+      inc[j] = (k0 + j) % n3;
+    }
     for (int l = 0; l < n3; ++l) {
       const size_t src = transposed ? ((size_t)s + (size_t)r * ((size_t)i + (size_t)n * l))
                                     : ((size_t)i + (size_t)n * ((size_t)s + (size_t)r * l));
       const T v = in[src];
-      const cx<T> w = twg[m];
-      acc[l & 3].re = fma(v, w.re, acc[l & 3].re);
-      acc[l & 3].im = fma(v, w.im, acc[l & 3].im);
-      m += k;
-      if (m >= n3) m -= n3;
+#pragma unroll
+      for (int j = 0; j < kFT; ++j) {
+        const cx<T> w = twg[m[j]];
+        acc[j].re = fma(v, w.re, acc[j].re);
+        acc[j].im = fma(v, w.im, acc[j].im);
+        m[j] += inc[j];
+        if (m[j] >= n3) m[j] -= n3;
+      }
     }
-    cx<T> v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-    if (k == 0 || 2 * k == n3) v.im = T(0);
-    out[e] = v;
+#pragma unroll
+    for (int j = 0; j < kFT; ++j) {
+      const int k = k0 + j;
+      if (k >= S) break;
+      cx<T> v = acc[j];
+      if (k == 0 || 2 * k == n3) v.im = T(0);
+      out[((size_t)k * r + s) * n + i] = v;
+    }
   }
 }
 
-// Inverse of k_factor_dft (Eq. (barAAk)) back to the caller's layout.
+// Inverse of k_factor_dft (Eq. (barAAk)) back to the caller's layout: each work
+// item is one tube (s, i) and kFT consecutive positions l.
 template <typename T>
 __global__ void k_factor_idft(const cx<T>* __restrict__ in, T* __restrict__ out, int n, int r, int n3, int transposed,
                               const cx<T>* __restrict__ twg) {
   const int S = n3 / 2 + 1;
   const bool even = (n3 % 2) == 0;
   const int kmax = even ? S - 2 : S - 1;
-  const size_t total = (size_t)n * r * n3;
+  const size_t total = (size_t)((n3 + kFT - 1) / kFT) * r * n;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    int i, s, l;
-    if (transposed) {
-      s = (int)(e % r);
-      i = (int)((e / r) % n);
-      l = (int)(e / ((size_t)r * n));
-    } else {
-      i = (int)(e % n);
-      s = (int)((e / n) % r);
-      l = (int)(e / ((size_t)n * r));
-    }
-    T acc[2] = {in[((size_t)0 * r + s) * n + i].re, T(0)};
-    int m = 0;  // k * l mod n3
+    int i, s;
+    size_t blk;
+    factor_item(e, n, r, 0, i, s, blk);  // i fastest: the spectrum [S][r][n] is read coalesced
+    const int l0 = (int)blk * kFT;
+    T acc[kFT];
+    const T s0 = in[(size_t)s * n + i].re;
+#pragma unroll
+    for (int j = 0; j < kFT; ++j) acc[j] = s0;
+    int base = 0;  // k l0 mod n3
     for (int k = 1; k <= kmax; ++k) {
-      m += l;
-      if (m >= n3) m -= n3;
+      base += l0;
+      if (base >= n3) base -= n3;
       const cx<T> v = in[((size_t)k * r + s) * n + i];
-      const cx<T> w = twg[m];
-      // 2 Re(v exp(+i 2 pi k l / n3)) = 2 (v.re w.re + v.im w.im)
-      acc[k & 1] = fma(T(2) * v.re, w.re, fma(T(2) * v.im, w.im, acc[k & 1]));
+      int idx = base;  // k (l0 + j) mod n3
+#pragma unroll
+      for (int j = 0; j < kFT; ++j) {
+        const cx<T> w = twg[idx];
+        // 2 Re(v exp(+i 2 pi k l / n3)) = 2 (v.re w.re + v.im w.im)
+        acc[j] = fma(T(2) * v.re, w.re, fma(T(2) * v.im, w.im, acc[j]));
+        idx += k;
+        if (idx >= n3) idx -= n3;
+      }
     }
-    if (even) {
-      const T nyq = in[((size_t)(S - 1) * r + s) * n + i].re;
-      acc[0] += (l & 1) ? -nyq : nyq;
+    const T nyq = even ? in[((size_t)(S - 1) * r + s) * n + i].re : T(0);
+#pragma unroll
+    for (int j = 0; j < kFT; ++j) {
+      const int l = l0 + j;
+      if (l >= n3) break;
+      T a = acc[j];
+      if (even) a += (l & 1) ? -nyq : nyq;
+      const size_t dst = transposed ? ((size_t)s + (size_t)r * ((size_t)i + (size_t)n * l))
+                                    : ((size_t)i + (size_t)n * ((size_t)s + (size_t)r * l));
+      out[dst] = a / T(n3);
     }
-    out[e] = (acc[0] + acc[1]) / T(n3);
   }
 }
 
@@ -121,69 +162,57 @@ __global__ void k_check(Dev<T> d) {
   }
 }
 
-// rho1 term of f0 per slice, tr(B A) with B = (H X~)^H (H X~) and A = Y~ Y~^H
-// (||H Z~_k||_F^2 for Z~_k = X~_k Y~_k, Eq. (HunfZ2)).  One CTA per slice; each
-// upper-triangle pair (s, u) of the two r x r Grams is summed by tp adjacent
-// threads that split the rows, with products in the working precision
-// accumulated error-free (dot2: about twice the working precision) and the
-// partial sums combined in FP64; the trace is accumulated in FP64 as
-// sum_s B_ss A_ss + 2 sum_{s<u} Re(B_su A_us).
-template <typename T>
-__device__ __forceinline__ void cdot2_acc(T (&acc)[4], cx<T> a, cx<T> b) {
-  // conj(a) b = (ar br + ai bi) + i (ar bi - ai br), four error-free running sums
-  dot2(acc[0], acc[2], a.re, b.re);
-  dot2(acc[0], acc[2], a.im, b.im);
-  dot2(acc[1], acc[3], a.re, b.im);
-  dot2(acc[1], acc[3], -a.im, b.re);
-}
+// rho1 term of f0 per slice: ||H Z~_k||_F^2 (Eq. (HunfZ2)), the sum over rows of
+// |Z~_k(i+1, :) - Z~_k(i, :)|^2 of the stored spectrum Z~ = X~Y~ of the current
+// factors; equal to tr((H X~)^H (H X~) Y~ Y~^H).  Grid (S, kRhoChunks): CTA
+// (k, c) streams chunk c of the slice's row differences (coalesced along n2)
+// and writes part_k[k kRhoChunks + c]; squares are summed error-free per thread
+// (dot2) and the thread totals added in FP64 in a fixed order.
+constexpr int kRhoChunks = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rho1_term(Dev<T> d) {
   __shared__ double part[32];
-  const int k = blockIdx.x;
-  const int n1 = d.n1, n2 = d.n2, r = d.r;
-  const int ntask = r * (r + 1) / 2;
-  const cx<T>* X = d.Xt + (size_t)k * r * n1;
-  const cx<T>* Y = d.Yt + (size_t)k * r * n2;
-  int tp = 1;
-  while (tp < 32 && tp * 2 * ntask <= (int)blockDim.x) tp *= 2;
-  const int per_pass = blockDim.x / tp, q = threadIdx.x & (tp - 1);
-  double tot = 0.0;
-  for (int base = 0; base < ntask; base += per_pass) {  // every thread runs the same passes
-    const int task = base + (int)threadIdx.x / tp;
-    double bre = 0.0, bim = 0.0, are = 0.0, aim = 0.0;
-    int s = 0, u = 0;
-    if (task < ntask) {
-      tri_index(task, r, s, u);
-      T b[4] = {T(0), T(0), T(0), T(0)}, a[4] = {T(0), T(0), T(0), T(0)};
-      const cx<T>* xs = X + (size_t)s * n1;
-      const cx<T>* xu = X + (size_t)u * n1;
-      for (int i = q; i + 1 < n1; i += tp) cdot2_acc(b, xs[i] - xs[i + 1], xu[i] - xu[i + 1]);  // B_su
-      const cx<T>* ys = Y + (size_t)s * n2;
-      const cx<T>* yu = Y + (size_t)u * n2;
-      for (int j = q; j < n2; j += tp) cdot2_acc(a, ys[j], yu[j]);  // conj(y_s) y_u summed: A_us
-      bre = (double)b[0] + (double)b[2];
-      bim = (double)b[1] + (double)b[3];
-      are = (double)a[0] + (double)a[2];
-      aim = (double)a[1] + (double)a[3];
+  const int k = blockIdx.x, ch = blockIdx.y;
+  const int n1 = d.n1, n2 = d.n2;
+  const size_t rs = (size_t)d.S * n2;  // distance between rows i and i + 1 of slice k
+  const cx<T>* Z = d.Zt + (size_t)k * n2;
+  T s = T(0), c = T(0);
+  const int nd = n1 > 1 ? n1 - 1 : 0, per = (nd + kRhoChunks - 1) / kRhoChunks;
+  const int i0 = min(ch * per, nd), i1 = min(i0 + per, nd);
+  // a thread walks down column j through the chunk's rows, keeping the previous
+  // row's value, so each entry is read once; four rows are loaded at a time
+  for (int j = threadIdx.x; j < n2 && i0 < i1; j += blockDim.x) {
+    cx<T> prev = Z[(size_t)i0 * rs + j];
+    int i = i0;
+    for (; i + 4 <= i1; i += 4) {
+      cx<T> nx[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) nx[q] = Z[(size_t)(i + 1 + q) * rs + j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const cx<T> a = nx[q] - prev;
+        dot2(s, c, a.re, a.re);
+        dot2(s, c, a.im, a.im);
+        prev = nx[q];
+      }
     }
-    for (int o = tp >> 1; o > 0; o >>= 1) {
-      bre += __shfl_xor_sync(0xffffffffu, bre, o);
-      bim += __shfl_xor_sync(0xffffffffu, bim, o);
-      are += __shfl_xor_sync(0xffffffffu, are, o);
-      aim += __shfl_xor_sync(0xffffffffu, aim, o);
+    for (; i < i1; ++i) {
+      const cx<T> cur = Z[(size_t)(i + 1) * rs + j];
+      const cx<T> a = cur - prev;
+      dot2(s, c, a.re, a.re);
+      dot2(s, c, a.im, a.im);
+      prev = cur;
     }
-    // B_su = sum_i conj(Hx_s) Hx_u = (bre, bim); A_us = sum_j y_u conj(y_s) = (are, aim)
-    if (task < ntask && q == 0) tot += (s == u ? 1.0 : 2.0) * (bre * are - bim * aim);
   }
-  tot = warp_sum(tot);
+  double tot_d = warp_sum((double)s + (double)c);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) part[wid] = tot;
+  if (lane == 0) part[wid] = tot_d;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += part[w];
-    d.part_k[k] = sum;
+    d.part_k[(size_t)k * kRhoChunks + ch] = sum;
   }
 }
 
@@ -205,6 +234,16 @@ __global__ void __launch_bounds__(256) k_rho1_term(Dev<T> d) {
 // values) and its eigendecomposition is the block Jacobi in FP64.  Shared
 // memory: rank_smem_bytes(r).
 // ---------------------------------------------------------------------------
+// s/c running sums of conj(a) b = (ar br + ai bi) + i (ar bi - ai br): acc[0],
+// acc[1] the real and imaginary sums, acc[2], acc[3] their error terms (dot2).
+template <typename T>
+__device__ __forceinline__ void cdot2_acc(T (&acc)[4], cx<T> a, cx<T> b) {
+  dot2(acc[0], acc[2], a.re, b.re);
+  dot2(acc[0], acc[2], a.im, b.im);
+  dot2(acc[1], acc[3], a.re, b.im);
+  dot2(acc[1], acc[3], -a.im, b.re);
+}
+
 __host__ __device__ inline size_t rank_smem_bytes(int r) {
   return (7 * (size_t)r * r + 3 * (size_t)r + 2) * sizeof(cx<double>) + 2 * 32 * sizeof(int);
 }

@@ -73,63 +73,26 @@ __host__ inline size_t dcon_smem_bytes(int n1, int r, int rp, bool x_in_smem = t
   return ((size_t)(kYThreads / 32) * rp * 32 + (x_in_smem ? (size_t)r * n1 : 0)) * sizeof(cx<T>);
 }
 
-// The rho1 terms, one CTA per slice, added in place:
-//   GX (= R~Y~^H, [S][r][n1]) += rho1 (H^T H X~) A,   A = Y~ Y~^H
-//   GY (= X~^H R~, [S][r][n2]) += rho1 B Y~,          B = (H X~)^H (H X~)
-// Shared memory: A and B (2 r^2 complex).
+// rho1 part of the gradient: with E = P_Omega(Z - G) + rho1 (H^T H) x_1 Z the
+// spectrum R~ holds DFT3(P_Omega(Z - G)) after the slab kernel; adding
+// rho1 (H^T H Z~)_k to every slice makes the contractions R~Y~^H and X~^H R~
+// that follow give the whole gradient.  (H^T H z)_i = deg_i z_i - z_{i-1} -
+// z_{i+1} along mode 1.  One thread per entry of R~ ([n1][S][n2]).
 template <typename T>
-__global__ void __launch_bounds__(kSliceThreads) k_grad_rho1(Dev<T> d, cx<T>* __restrict__ GX, cx<T>* __restrict__ GY) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int k = blockIdx.x;
-  const int n1 = d.n1, n2 = d.n2, r = d.r, rr = r * r;
-  const int tid = threadIdx.x;
+__global__ void k_grad_hth(Dev<T> d) {
+  const int n1 = d.n1, n2 = d.n2, S = d.S;
+  const size_t rs = (size_t)S * n2, tot = (size_t)n1 * rs;
   const T rho1 = d.rho1;
-  cx<T>* A = reinterpret_cast<cx<T>*>(smem);
-  cx<T>* B = A + rr;
-  const cx<T>* X = d.Xt + (size_t)k * r * n1;
-  const cx<T>* Y = d.Yt + (size_t)k * r * n2;
-  // Grams: tp adjacent threads per (s, u) pair, partial sums combined by shuffles
-  int tp = 1;
-  while (tp < 32 && tp * 2 * rr <= (int)blockDim.x) tp *= 2;
-  const int per_pass = blockDim.x / tp;
-  for (int base = 0; base < rr; base += per_pass) {
-    const int task = base + tid / tp, q = tid & (tp - 1);
-    const bool has = task < rr;
-    const int s = has ? task / r : 0, u = has ? task - s * r : 0;
-    cx<T> a = {T(0), T(0)}, b = {T(0), T(0)};
-    if (has) {
-      for (int j = q; j < n2; j += tp) cfmac(a, Y[(size_t)s * n2 + j], Y[(size_t)u * n2 + j]);
-      for (int i = q; i + 1 < n1; i += tp)
-        cfmaconj(b, X[(size_t)s * n1 + i] - X[(size_t)s * n1 + i + 1], X[(size_t)u * n1 + i] - X[(size_t)u * n1 + i + 1]);
-    }
-    for (int o = tp >> 1; o > 0; o >>= 1) {
-      a.re += __shfl_xor_sync(0xffffffffu, a.re, o);
-      a.im += __shfl_xor_sync(0xffffffffu, a.im, o);
-      b.re += __shfl_xor_sync(0xffffffffu, b.re, o);
-      b.im += __shfl_xor_sync(0xffffffffu, b.im, o);
-    }
-    if (has && q == 0) {
-      A[s * r + u] = a;
-      B[s * r + u] = b;
-    }
-  }
-  __syncthreads();
-  const bool realslice = (k == 0) || (2 * k == d.n3);
-  for (int e = tid; e < r * n1; e += blockDim.x) {
-    const int s = e / n1, i = e - s * n1;
-    cx<T> acc = {T(0), T(0)};
-    for (int u = 0; u < r; ++u) cfma(acc, hth_at(X + (size_t)u * n1, i, n1), A[u * r + s]);
-    cx<T> v = GX[(size_t)k * r * n1 + e] + acc * rho1;
-    if (realslice) v.im = T(0);
-    GX[(size_t)k * r * n1 + e] = v;
-  }
-  for (int e = tid; e < r * n2; e += blockDim.x) {
-    const int s = e / n2, j = e - s * n2;
-    cx<T> acc = {T(0), T(0)};
-    for (int u = 0; u < r; ++u) cfma(acc, B[s * r + u], Y[(size_t)u * n2 + j]);
-    cx<T> v = GY[(size_t)k * r * n2 + e] + acc * rho1;
-    if (realslice) v.im = T(0);
-    GY[(size_t)k * r * n2 + e] = v;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / rs);
+    const cx<T> z = d.Zt[e];
+    cx<T> h = {T(0), T(0)};
+    if (i > 0) h = h + (z - d.Zt[e - rs]);
+    if (i + 1 < n1) h = h + (z - d.Zt[e + rs]);
+    const int k = (int)((e / n2) % S);
+    cx<T> v = d.Rt[e] + h * rho1;
+    if (k == 0 || 2 * k == d.n3) v.im = T(0);
+    d.Rt[e] = v;
   }
 }
 

@@ -222,7 +222,7 @@ class Engine final : public EngineBase {
     T* hinv = alloc<T>((size_t)2 * n1_, err);
     cx<T>* twg = alloc<cx<T>>((size_t)n3_, err);
     double* part = alloc<double>((size_t)n1_ * 4, err);
-    double* part_k = alloc<double>((size_t)S_, err);
+    double* part_k = alloc<double>((size_t)S_ * kRhoChunks, err);
     int* derr = alloc<int>(1, err);
     // stopping test (eps > 0): change maxima, flag, counter; |dW| partial sums; Z~ changes
     unsigned long long* conv = nullptr;
@@ -548,9 +548,9 @@ class Engine final : public EngineBase {
     }
     launch_slab(MODE_R, nullptr, 0, stream_);
     launch_slab(MODE_W, nullptr, 0, stream_);
-    k_rho1_term<T><<<S_, 256, 0, stream_>>>(d_);
+    k_rho1_term<T><<<dim3(S_, kRhoChunks), 256, 0, stream_>>>(d_);
     TC_CUDA_TRY(cudaGetLastError());
-    std::vector<double> part((size_t)n1_ * 4), pk(S_);
+    std::vector<double> part((size_t)n1_ * 4), pk((size_t)S_ * kRhoChunks);
     TC_CUDA_TRY(cudaMemcpyAsync(part.data(), d_.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
     TC_CUDA_TRY(cudaMemcpyAsync(pk.data(), d_.part_k, pk.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
     TC_CUDA_TRY(cudaStreamSynchronize(stream_));
@@ -565,7 +565,9 @@ class Engine final : public EngineBase {
     }
     for (int k = 0; k < S_; ++k) {
       const double c = (k == 0 || 2 * k == n3_) ? 1.0 : 2.0;
-      sh += c * pk[k];
+      double v = 0.0;
+      for (int q = 0; q < kRhoChunks; ++q) v += pk[(size_t)k * kRhoChunks + q];
+      sh += c * v;
     }
     // f0 of Eq. (TETP-optim): ||Z - W||^2 = ||R||^2; the rho1 term by Parseval
     // from the factors (Eq. (HunfZ2))

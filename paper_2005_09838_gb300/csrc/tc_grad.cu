@@ -165,7 +165,7 @@ struct GradEngine final : tc_grad {
     GY_ = alloc<cx<T>>((size_t)S_ * r_ * n2_, err);
     cx<T>* twg = alloc<cx<T>>((size_t)n3_, err);
     double* part = alloc<double>((size_t)n1_ * 4, err);
-    double* part_k = alloc<double>((size_t)S_, err);
+    double* part_k = alloc<double>((size_t)S_ * kRhoChunks, err);
     int* derr = alloc<int>(1, err);
     xin_ = alloc<T>((size_t)n1_ * r_ * n3_, err);
     yin_ = alloc<T>((size_t)r_ * n2_ * n3_, err);
@@ -262,12 +262,15 @@ struct GradEngine final : tc_grad {
       k_synth_init<T><<<(unsigned)std::min<size_t>((tot + 255) / 256, 8 * 152), 256, 0, stream_>>>(d_);
     }
     slab_.f<<<n1_, slab_.threads, slab_.smem, stream_>>>(d_, nullptr, slab_.in_smem ? 1 : 0, 0);  // R~, ||E||^2
-    if (d_.rho1 != T(0)) k_rho1_term<T><<<S_, 256, 0, stream_>>>(d_);
+    if (d_.rho1 != T(0)) k_rho1_term<T><<<dim3(S_, kRhoChunks), 256, 0, stream_>>>(d_);  // ||H Z~_k||^2 from Z~
     if (dX || dY) {
+      if (d_.rho1 != T(0)) {
+        // R~ += rho1 H^T H Z~: the contractions below then carry the rho1 term too
+        const size_t tot = (size_t)n1_ * S_ * n2_;
+        k_grad_hth<T><<<(unsigned)std::min<size_t>((tot + 255) / 256, 16 * 152), 256, 0, stream_>>>(d_);
+      }
       qcon_<<<dim3(S_, (n1_ + 31) / 32), kSliceThreads, qsmem_, stream_>>>(d_, GX_);  // R~ Y~^H
       dcon_<<<dim3(S_, (n2_ + 31) / 32), kYThreads, dsmem_, stream_>>>(d_, GY_);     // X~^H R~
-      if (d_.rho1 != T(0))
-        k_grad_rho1<T><<<S_, kSliceThreads, 2 * (size_t)r_ * r_ * sizeof(cx<T>), stream_>>>(d_, GX_, GY_);
       T* ox = static_cast<T*>(dX);
       T* oy = static_cast<T*>(dY);
       if (!on_device) {
@@ -282,7 +285,7 @@ struct GradEngine final : tc_grad {
       }
     }
     TCG_TRY(cudaGetLastError());
-    std::vector<double> part(4 * (size_t)n1_), pk(S_);
+    std::vector<double> part(4 * (size_t)n1_), pk((size_t)S_ * kRhoChunks);
     TCG_TRY(cudaMemcpyAsync(part.data(), d_.part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
     if (d_.rho1 != T(0))
       TCG_TRY(cudaMemcpyAsync(pk.data(), d_.part_k, pk.size() * sizeof(double), cudaMemcpyDeviceToHost, stream_));
@@ -297,7 +300,11 @@ struct GradEngine final : tc_grad {
     for (int i = 0; i < n1_; ++i) e2 += part[4 * (size_t)i];
     double h2 = 0.0;  // sum over all n3 slices of ||H Z~_k||^2 (half spectrum, mirrored slices twice)
     if (d_.rho1 != T(0))
-      for (int k = 0; k < S_; ++k) h2 += ((k == 0 || 2 * k == n3_) ? 1.0 : 2.0) * pk[k];
+      for (int k = 0; k < S_; ++k) {
+        double v = 0.0;
+        for (int q = 0; q < kRhoChunks; ++q) v += pk[(size_t)k * kRhoChunks + q];
+        h2 += ((k == 0 || 2 * k == n3_) ? 1.0 : 2.0) * v;
+      }
     const double f = 0.5 * e2 + 0.5 * (double)d_.rho1 * h2 / (double)n3_;
     if (!std::isfinite(f)) {
       err = "loss is not finite";

@@ -46,7 +46,7 @@ struct Dev {
   const cx<T>* twg; // [n3] exp(-2 pi i m / n3) for the generic transform
   T* scratch;       // per-CTA slabs when shared memory is too small
   double* part;     // [n1][4] objective partial sums
-  double* part_k;   // [S] rho1-term per slice
+  double* part_k;   // [S][kRhoChunks] rho1-term partial sums per slice
   int* err;
   double rtol;
   // step control (Eq. (updataXYW1) step sizes; Algorithm step 6)

@@ -107,7 +107,11 @@ __global__ void k_static_objective(const double* part, const double* part_k, int
     sw += part[(size_t)i * 4 + 2];
     sk += part[(size_t)i * 4 + 3];
   }
-  for (int k = 0; k < S; ++k) sh += ((k == 0 || 2 * k == n3) ? 1.0 : 2.0) * part_k[k];
+  for (int k = 0; k < S; ++k) {
+    double pk = 0.0;
+    for (int c = 0; c < kRhoChunks; ++c) pk += part_k[(size_t)k * kRhoChunks + c];
+    sh += ((k == 0 || 2 * k == n3) ? 1.0 : 2.0) * pk;
+  }
   out[0] = 0.5 * sr + 0.5 * mu * sw + 0.5 * rho2 * sk + 0.5 * rho1 * sh / (double)n3;
 }
 
@@ -160,7 +164,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   T* hinv = cv.take<T>((size_t)2 * n1);
   cx<T>* twg = cv.take<cx<T>>((size_t)n3);
   d.part = cv.take<double>((size_t)n1 * 4);
-  d.part_k = cv.take<double>((size_t)S);
+  d.part_k = cv.take<double>((size_t)S * kRhoChunks);
   double* fout = cv.take<double>(1);
   d.err = cv.take<int>(1);
   d.scratch = slabs_in_smem ? nullptr : cv.take<T>(lay.slab_bytes / sizeof(T) * (size_t)n1 + 16);
@@ -239,7 +243,7 @@ tc_status run_static(const tc_params& p, const void* G, const uint8_t* mask, con
   slab[MODE_W]<<<n1, 256, lay.total, st>>>(d, static_cast<T*>(W), sis, 0);
   if (f0) {
     slab[MODE_R]<<<n1, 256, lay.total, st>>>(d, nullptr, sis, 0);
-    k_rho1_term<T><<<S, 256, 0, st>>>(d);
+    k_rho1_term<T><<<dim3(S, kRhoChunks), 256, 0, st>>>(d);
     k_static_objective<<<1, 32, 0, st>>>(d.part, d.part_k, n1, S, n3, p.mu, p.rho1, p.rho2, fout);
   }
   cudaError_t e = cudaGetLastError();
