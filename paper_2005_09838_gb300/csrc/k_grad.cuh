@@ -5,10 +5,11 @@
 // With E = P_Omega(Z - G) + rho1 (H^T H) x_1 Z, Z = X*Y, the gradients are the
 // t-products dL/dX = E * Y^* and dL/dY = X^* * E (conjugate transpose of
 // Sec. 2), i.e. per slice of the half spectrum
-//   dL/dX~_k = E~_k Y~_k^H = R~_k Y~_k^H + rho1 H^T H X~_k (Y~_k Y~_k^H),
-//   dL/dY~_k = X~_k^H E~_k = X~_k^H R~_k + rho1 (X~_k^H H^T H X~_k) Y~_k,
-// with R~ = DFT(P_Omega(Z - G)) from the slab kernel (MODE_GRAD); the
-// inverse mode-3 DFT brings them back to the spatial factors.
+//   dL/dX~_k = E~_k Y~_k^H,  dL/dY~_k = X~_k^H E~_k,
+// E~_k = R~_k + rho1 H^T H Z~_k with R~ = DFT(P_Omega(Z - G)) from the slab
+// kernel (MODE_GRAD) and the stencil k_grad_hth adding the rho1 part in
+// place; the inverse mode-3 DFT brings the gradients back to the spatial
+// factors.
 #pragma once
 
 namespace tc {
