@@ -43,18 +43,44 @@ __device__ inline T warp_frob(const cx<T>* M, int ld, int col0, int r) {
   return sqrt(s);
 }
 
+// Frobenius norms in FP32 without overflow, underflow, divisions or branches:
+// a pair (e, sq) stands for 2^e sqrt(sq), the entries scaled by 2^-e staying
+// below 2 (e the largest binary exponent seen, clamped to the normal range).
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((min(max(k, -126), 127) + 127) << 23); }
+__device__ __forceinline__ void nrm_add(int& e, float& sq, float x) {
+  const int ex = min(((__float_as_int(x) >> 23) & 0xff) - 126, 126);  // |x| < 2^ex
+  const int en = max(e, ex);
+  const float t = fabsf(x) * pow2f(-en);
+  sq = fmaf(t, t, sq * pow2f(2 * (e - en)));
+  e = en;
+}
+__device__ __forceinline__ void nrm_merge(int& e, float& sq, int e2, float sq2) {
+  const int en = max(e, e2);
+  sq = sq * pow2f(2 * (e - en)) + sq2 * pow2f(2 * (e2 - en));
+  e = en;
+}
+__device__ __forceinline__ void warp_nrm(int& e, float& sq) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const int e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    const float q2 = __shfl_xor_sync(0xffffffffu, sq, o);
+    nrm_merge(e, sq, e2, q2);
+  }
+}
+constexpr int kNrmE0 = -126;  // the empty pair: (kNrmE0, 0)
+
 // The same in FP32 arithmetic (a certificate needs only a few digits; the
-// FP64 pipe of this part is slow).
+// FP64 pipe of this part is slow), as a scaled sum of squares.
 template <typename T>
 __device__ inline float warp_frob_lowp(const cx<T>* M, int r) {
   const int lane = threadIdx.x & 31;
-  float s = 0.f;
+  int ex = kNrmE0;
+  float sq = 0.f;
   for (int e = lane; e < r * r; e += 32) {
-    const float a = (float)M[e].re, b = (float)M[e].im;
-    s = fmaf(a, a, fmaf(b, b, s));
+    nrm_add(ex, sq, (float)M[e].re);
+    nrm_add(ex, sq, (float)M[e].im);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return sqrtf(s);
+  warp_nrm(ex, sq);
+  return sqrtf(sq) * pow2f(ex);  // infinite beyond the FP32 range
 }
 
 // 1/a.  FP64: a correctly rounded FP32 seed and two Newton steps
@@ -292,10 +318,302 @@ __device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in)
   return 1;
 }
 
-// DF: the block inverse (r > 16) of an FP64 matrix runs in df64 arithmetic.
+// Barrier 1 among the first n threads of the block (n a multiple of 32).
+__device__ __forceinline__ void bar_first(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
+// Static shared scratch of the register eliminations and of the norm
+// reduction of herm_inverse_refined (used one after the other), independent
+// of the callers' dynamic carve; within the kStaticSmemReserve headroom.
+static __shared__ float g_solve_xch[256];
+
+// Gauss-Jordan inverse without pivoting (the update rules of
+// gauss_jordan_inplace) of an r x r matrix, r <= 32, with the matrix in
+// registers: lane j holds column j, warp w rows RPL w .. RPL w + RPL - 1
+// (ceil(r / RPL) warps), padded with the identity beyond r.  At pivot p the
+// warp holding row p scales it by the pivot's reciprocal and passes it on
+// through shared memory (two buffers, so one barrier of those warps per pivot
+// suffices); each warp takes column p of its rows from lane p by shuffles.
+// Every candidate value is formed by every lane and selected, so no branch
+// diverges.  A warp runs this serial chain at well under one instruction per
+// clock, so two rows per lane (sixteen warps at r = 32) are used where the
+// block has the warps.  The other warps only meet the final __syncthreads.
+// Exchange area: g_solve_xch.  Returns 1 (block-uniform) unless a pivot is
+// not positive.  ld: row pitch of Ainv.  Every thread of the block calls it.
+template <int RPL>
+static __device__ __noinline__ int gj_regs_cf_t(const cx<float>* A, cx<float>* Ainv, int r, int ld) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float* xch = g_solve_xch;
+  cx<float>* trow = reinterpret_cast<cx<float>*>(xch);  // [2][32] scaled pivot rows
+  float* prc = xch + 128;                                // [2] pivot reciprocals
+  int* okf = reinterpret_cast<int*>(xch + 130);
+  const int nwu = (r + RPL - 1) / RPL;
+  if (w < nwu) {
+    cx<float> a[RPL];
+#pragma unroll
+    for (int m = 0; m < RPL; ++m) {
+      const int i = RPL * w + m;
+      a[m] = (i < r && lane < r) ? A[i * r + lane] : cx<float>{i == lane ? 1.f : 0.f, 0.f};
+    }
+    int ok = 1;
+    for (int p = 0; p < r; ++p) {
+      const int b = p & 1;
+      if (w == p / RPL) {
+        cx<float> rp = a[0];
+#pragma unroll
+        for (int m = 1; m < RPL; ++m)
+          if (m == p % RPL) rp = a[m];
+        const float pv = __shfl_sync(0xffffffffu, rp.re, p);
+        const bool good = pv > tiny_pivot<float>() && isfinite(pv);
+        const float ip = good ? __frcp_rn(pv) : 0.f;
+        trow[b * 32 + lane] = rp * ip;
+        if (lane == 0) prc[b] = ip;
+      }
+      bar_first(32 * nwu);
+      const float ip = prc[b];
+      if (ip == 0.f) {
+        ok = 0;
+        break;
+      }
+      const cx<float> t = trow[b * 32 + lane];
+      const bool lp = lane == p;
+#pragma unroll
+      for (int m = 0; m < RPL; ++m) {
+        const cx<float> c = {__shfl_sync(0xffffffffu, a[m].re, p), __shfl_sync(0xffffffffu, a[m].im, p)};
+        const cx<float> u = a[m] - cmul(c, t);
+        const bool rp = RPL * w + m == p;
+        const float vr = lp ? (rp ? ip : -c.re * ip) : (rp ? t.re : u.re);
+        const float vi = lp ? (rp ? 0.f : -c.im * ip) : (rp ? t.im : u.im);
+        a[m] = cx<float>{vr, vi};
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < RPL; ++m) {
+      const int i = RPL * w + m;
+      if (i < r && lane < r) Ainv[i * ld + lane] = a[m];
+    }
+    if (tid == 0) *okf = ok;
+  }
+  __syncthreads();
+  return *okf;
+}
+static __device__ __forceinline__ int gj_regs_cf(const cx<float>* A, cx<float>* Ainv, int r, int ld) {
+  return (int)blockDim.x >= 32 * ((r + 1) / 2) ? gj_regs_cf_t<2>(A, Ainv, r, ld) : gj_regs_cf_t<8>(A, Ainv, r, ld);
+}
+
+// The same for a real r x r matrix in df64 arithmetic (FP64 in and out, pitch
+// r); also leaves ||A||_F and ||A^-1||_F (FP32, a certificate needs a few
+// digits; infinite beyond the FP32 range) in g_solve_xch[200], [201].
+template <int RPL>
+static __device__ __noinline__ int gj_regs_df_t(const double* A, double* Ainv, int r) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float* xch = g_solve_xch;
+  df* trow = reinterpret_cast<df*>(xch);  // [2][32]
+  df* prc = trow + 64;                    // [2]
+  int* okf = reinterpret_cast<int*>(xch + 132);
+  int* xe = reinterpret_cast<int*>(xch + 136);  // [16][4] per-warp norm pairs
+  const int nwu = (r + RPL - 1) / RPL;
+  if (w < nwu) {
+    df a[RPL];
+    int ae = kNrmE0;
+    float aq = 0.f;
+#pragma unroll
+    for (int m = 0; m < RPL; ++m) {
+      const int i = RPL * w + m;
+      a[m] = (i < r && lane < r) ? df_from(A[i * r + lane]) : df{i == lane ? 1.f : 0.f, 0.f};
+      if (i < r && lane < r) nrm_add(ae, aq, a[m].hi);
+    }
+    int ok = 1;
+    for (int p = 0; p < r; ++p) {
+      const int b = p & 1;
+      if (w == p / RPL) {
+        df rp = a[0];
+#pragma unroll
+        for (int m = 1; m < RPL; ++m)
+          if (m == p % RPL) rp = a[m];
+        const df pv = {__shfl_sync(0xffffffffu, rp.hi, p), __shfl_sync(0xffffffffu, rp.lo, p)};
+        const bool good = pv.hi > 1e-30f && isfinite(pv.hi);
+        const df ip = good ? df_rcp(pv) : df{0.f, 0.f};
+        trow[b * 32 + lane] = df_mul(rp, ip);
+        if (lane == 0) prc[b] = ip;
+      }
+      bar_first(32 * nwu);
+      const df ip = prc[b];
+      if (!(ip.hi > 0.f)) {
+        ok = 0;
+        break;
+      }
+      const df t = trow[b * 32 + lane];
+      const bool lp = lane == p;
+#pragma unroll
+      for (int m = 0; m < RPL; ++m) {
+        const df c = {__shfl_sync(0xffffffffu, a[m].hi, p), __shfl_sync(0xffffffffu, a[m].lo, p)};
+        const df u = df_add(a[m], df_neg(df_mul(c, t)));
+        const df cq = df_neg(df_mul(c, ip));
+        const bool rp = RPL * w + m == p;
+        a[m] = df{lp ? (rp ? ip.hi : cq.hi) : (rp ? t.hi : u.hi), lp ? (rp ? ip.lo : cq.lo) : (rp ? t.lo : u.lo)};
+      }
+    }
+    int ie = kNrmE0;
+    float iq = 0.f;
+#pragma unroll
+    for (int m = 0; m < RPL; ++m) {
+      const int i = RPL * w + m;
+      if (i < r && lane < r) {
+        Ainv[i * r + lane] = df_to(a[m]);
+        nrm_add(ie, iq, a[m].hi);
+      }
+    }
+    warp_nrm(ae, aq);
+    warp_nrm(ie, iq);
+    if (lane == 0) {
+      xe[4 * w] = ae;
+      xch[137 + 4 * w] = aq;
+      xe[4 * w + 2] = ie;
+      xch[139 + 4 * w] = iq;
+    }
+    bar_first(32 * nwu);
+    if (w == 0) {  // lane q merges warp q's pairs
+      int e1 = kNrmE0, e2 = kNrmE0;
+      float q1 = 0.f, q2 = 0.f;
+      if (lane < nwu) {
+        e1 = xe[4 * lane];
+        q1 = xch[137 + 4 * lane];
+        e2 = xe[4 * lane + 2];
+        q2 = xch[139 + 4 * lane];
+      }
+      warp_nrm(e1, q1);
+      warp_nrm(e2, q2);
+      if (lane == 0) {
+        xch[200] = sqrtf(q1) * pow2f(e1);
+        xch[201] = sqrtf(q2) * pow2f(e2);
+        *okf = ok;
+      }
+    }
+  }
+  __syncthreads();
+  return *okf;
+}
+static __device__ __forceinline__ int gj_regs_df(const double* A, double* Ainv, int r) {
+  return (int)blockDim.x >= 32 * ((r + 1) / 2) ? gj_regs_df_t<2>(A, Ainv, r) : gj_regs_df_t<8>(A, Ainv, r);
+}
+
+// Inverse of a Hermitian positive definite r x r matrix A = Ah + Al (FP32 head
+// and tail, row-major, shared memory) to FP64-class accuracy on the FP32
+// pipes, for well-conditioned A: X0 = FP32 Gauss-Jordan inverse of Ah, then
+// one refinement step X1 = X0 + X0 R with the residual R = I - A X0 formed
+// from error-free products and compensated sums (Ogita-Rump-Oishi Dot2), so
+// that R is exact to a few units of 2^-48 |A| |X0|.  The error of X1 is about
+// ||R||^2 relative plus the FP32 rounding of the correction (2^-24 ||R||):
+// the step is accepted when ||R||_F <= 2^-14, which keeps it below 2^-27,
+// under the FP32 rounding every caller applies to the result, and when the
+// certificate ||A||_F ||A^-1||_F < 1/(2 rtol) holds (||A^-1||_F bounded by
+// ||X0||_F / (1 - ||R||_F)).  Returns 1 (block-uniform) with the Hermitian part
+// of X1 in Xo; 0 when a pivot is not positive or a test fails, and the caller
+// takes the df64 elimination or the eigendecomposition.  LO: Al is present
+// (else A = Ah exactly).  work: 3 r^2 values, red: 4 floats, shared memory;
+// every thread of the block calls it.
+template <bool LO>
+__device__ __noinline__ int herm_inverse_refined(const cx<float>* Ah, const cx<float>* Al, cx<float>* Xo,
+                                                 cx<float>* work, float* red, int r, double rtol) {
+  const int tid = threadIdx.x, nt = blockDim.x, rr = r * r;
+  cx<float>* X0 = work;          // r^2
+  cx<float>* C = work + rr;      // r^2: X0 R
+  cx<float>* R = work + 2 * rr;  // r^2
+  if (!gj_regs_cf(Ah, X0, r, r)) return 0;
+  // R = I - (Ah + Al) X0: Ah X0 by Dot2 (TwoProduct by FMA, TwoSum), Al X0 in
+  // FP32; the squared norms of R, X0 and Ah on the way
+  float nr = 0.f, xq = 0.f, aq = 0.f;
+  int xe = kNrmE0, ae = kNrmE0;
+  for (int e = tid; e < rr; e += nt) {
+    const int i = e / r, j = e - i * r;
+    const cx<float>* ah = Ah + i * r;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f, tr = 0.f, ti = 0.f;
+    for (int l = 0; l < r; ++l) {
+      const cx<float> a = ah[l], b = X0[l * r + j];
+      dot2(sr, cr, a.re, b.re);
+      dot2(sr, cr, -a.im, b.im);
+      dot2(si, ci, a.re, b.im);
+      dot2(si, ci, a.im, b.re);
+      if constexpr (LO) {
+        const cx<float> t = Al[i * r + l];
+        tr = fmaf(t.re, b.re, fmaf(-t.im, b.im, tr));
+        ti = fmaf(t.re, b.im, fmaf(t.im, b.re, ti));
+      }
+    }
+    // the diagonal: 1 - s is exact (s within a factor 2 of 1 once ||R|| is small)
+    const cx<float> v = {((i == j ? 1.f : 0.f) - sr) - (cr + tr), -si - (ci + ti)};
+    R[e] = v;
+    const cx<float> x = X0[e], a = Ah[e];
+    nr = fmaf(v.re, v.re, fmaf(v.im, v.im, nr));  // R is small: a plain sum
+    nrm_add(xe, xq, x.re);
+    nrm_add(xe, xq, x.im);
+    nrm_add(ae, aq, a.re);
+    nrm_add(ae, aq, a.im);
+  }
+  {
+    float* part = g_solve_xch;  // [32][5]
+    int* parti = reinterpret_cast<int*>(g_solve_xch);
+    for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    warp_nrm(xe, xq);
+    warp_nrm(ae, aq);
+    if ((tid & 31) == 0) {
+      const int w = tid >> 5;
+      part[5 * w] = nr;
+      parti[5 * w + 1] = xe;
+      part[5 * w + 2] = xq;
+      parti[5 * w + 3] = ae;
+      part[5 * w + 4] = aq;
+    }
+    __syncthreads();
+    if (tid < 32) {  // lane q merges warp q's partials
+      float sr = 0.f, q1 = 0.f, q2 = 0.f;
+      int e1 = kNrmE0, e2 = kNrmE0;
+      if (tid < ((nt + 31) >> 5)) {
+        sr = part[5 * tid];
+        e1 = parti[5 * tid + 1];
+        q1 = part[5 * tid + 2];
+        e2 = parti[5 * tid + 3];
+        q2 = part[5 * tid + 4];
+      }
+      for (int o = 16; o > 0; o >>= 1) sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      warp_nrm(e1, q1);
+      warp_nrm(e2, q2);
+      if (tid == 0) {
+        const float rn = sqrtf(sr);
+        // log2 of ||X0||_F ||A||_F against log2 of (1 - ||R||_F) / (2 rtol)
+        const float lhs = (float)(e1 + e2) + 0.5f * __log2f(q1 * q2);
+        const float rhs = __log2f((1.f - rn) * 0.5f) - __log2f((float)rtol);
+        red[0] = rn;
+        red[3] = (rn <= 0x1p-14f && q2 > 0.f && isfinite(lhs) && lhs < rhs) ? 1.f : 0.f;
+      }
+    }
+    __syncthreads();
+  }
+  if (red[3] == 0.f) return 0;
+  for (int e = tid; e < rr; e += nt) {
+    const int i = e / r, j = e - i * r;
+    cx<float> c = {0.f, 0.f};
+    for (int l = 0; l < r; ++l) cfma(c, X0[i * r + l], R[l * r + j]);
+    C[e] = c;
+  }
+  __syncthreads();
+  // Hermitian part of X1 = X0 + C; thread t takes (i, j) = (L, (L + c) mod r),
+  // L = t mod r, c = t / r, so that both the (i, j) and the (j, i) reads of a
+  // warp fall in distinct banks
+  for (int t = tid; t < rr; t += nt) {
+    const int c0 = t / r, i = t - c0 * r, j = (i + c0) % r;
+    const cx<float> a = X0[i * r + j], b = X0[j * r + i], c = C[i * r + j], g = C[j * r + i];
+    Xo[i * r + j] = cx<float>{0.5f * ((a.re + b.re) + (c.re + g.re)), 0.5f * ((a.im - b.im) + (c.im - g.im))};
+  }
+  __syncthreads();
+  return 1;
+}
+
+// DF: the block inverse (r > 16) of an FP64 matrix runs in df64 arithmetic,
+// after herm_inverse_refined on the FP32 split of A.
 template <typename T, int RP, bool DF = false>
 __device__ __noinline__ int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P, cx<T>* V, cx<T>* W, cx<T>* piv, T* sred,
-                                      int r, T rtol, bool force_eig = false) {
+                                      int r, T rtol, bool force_eig = false, bool refine = true) {
   const int tid = threadIdx.x, nt = blockDim.x;
   int ok;
   if (force_eig) {
@@ -326,6 +644,35 @@ __device__ __noinline__ int block_pinv_herm(const cx<T>* A, cx<T>* Ap, cx<T>* P,
       return 1;
     }
   } else {
+    if constexpr (DF && sizeof(T) == 8) {
+      if (refine) {
+        // A = Ah + Al in V (2 r^2 complex floats); the work of the refined inverse
+        // and its result in W (4 r^2 complex floats).  refine = false: the caller
+        // has tried it already.
+        const int rr = r * r;
+        cx<float>* ahf = reinterpret_cast<cx<float>*>(V);
+        cx<float>* alf = ahf + rr;
+        cx<float>* wf = reinterpret_cast<cx<float>*>(W);
+        cx<float>* xo = wf + 3 * rr;
+        for (int e = tid; e < rr; e += nt) {
+          const cx<T> a = A[e];
+          const cx<float> h = {(float)a.re, (float)a.im};
+          ahf[e] = h;
+          alf[e] = cx<float>{(float)(a.re - (T)h.re), (float)(a.im - (T)h.im)};
+        }
+        __syncthreads();
+        if (herm_inverse_refined<true>(ahf, alf, xo, wf, reinterpret_cast<float*>(sred), r, (double)rtol)) {
+          for (int e = tid; e < rr; e += nt) {
+            const int i = e / r, j = e - i * r;
+            Ap[e] = cx<T>{(T)xo[e].re, (T)xo[e].im};
+            P[e] = cx<T>{(i == j) ? T(1) : T(0), T(0)};
+          }
+          __syncthreads();
+          return 1;
+        }
+        __syncthreads();
+      }
+    }
     for (int e = tid; e < r * r; e += nt) W[e] = A[e];
     if (tid < 32) {
       const T an = DF ? (T)warp_frob_lowp(A, r) : warp_frob(A, r, 0, r);
@@ -925,7 +1272,7 @@ __device__ __forceinline__ cx<T> cvt(cx<S> v) {
 // of size 1/lambda_min; their rounding reaches the new Y~ amplified by that
 // condition number.  So on these slices G and Dg are accumulated with
 // error-free products and sums (the callers), the pseudo-inverse is taken in
-// df64 arithmetic with the FP64 path's cutoff (d.rtol64), and t G^+ is kept in
+// FP64 (df64 arithmetic for r > 16) with the FP64 path's cutoff (d.rtol64), and t G^+ is kept in
 // FP64 (d.Gp64, slot 0 for k = 0, slot 1 for the Nyquist slice) so that
 // k_ystep applies it in FP64.
 //
@@ -990,7 +1337,7 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
     jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);
     __syncthreads();
   }
-  // FP64 Gauss-Jordan on the real Gram, accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
+  // Gauss-Jordan on the real Gram (FP64; df64 for r > 16), accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
   // (then lambda_min > rtol lambda_max: nothing is cut, G^+ = G^-1); otherwise the
   // eigendecomposition fallback applies the cutoff
   // With the rank rule on (step 5), only the leading ra x ra block is active: the
@@ -1001,17 +1348,26 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
   double* pv = reinterpret_cast<double*>(piv64);    // 2
   for (int e = tid; e < ra2; e += nt) g[e] = G64[(e / ra) * r + e % ra].re;
   __syncthreads();
-  int ok = real_gj_fp64(g, wk, pv, ra);
-  if (tid < 32) {
-    double an = 0.0, in = 0.0;
-    for (int e = tid; e < ra2; e += 32) {
-      an += g[e] * g[e];
-      in += wk[e] * wk[e];
+  if (ra > 16) {
+    // df64 elimination in registers; the squared norms come with it (FP32)
+    const int ok = gj_regs_df(g, wk, ra);
+    if (tid == 0) {  // ||G||_F ||G^-1||_F < 1/(2 rtol)
+      const double an = g_solve_xch[200], in = g_solve_xch[201];
+      sred[1] = (ok && isfinite(in) && isfinite(an) && an * in < 0.5 / rtol) ? 1.0 : 0.0;
     }
-    an = warp_sum(an);
-    in = warp_sum(in);
-    // ||G||_F ||G^-1||_F < 1/(2 rtol), compared squared
-    if (tid == 0) sred[1] = (ok && isfinite(in) && an * in < 0.25 / (rtol * rtol)) ? 1.0 : 0.0;
+  } else {
+    const int ok = real_gj_fp64(g, wk, pv, ra);  // every thread of the block
+    if (tid < 32) {
+      double an = 0.0, in = 0.0;
+      for (int e = tid; e < ra2; e += 32) {
+        an += g[e] * g[e];
+        in += wk[e] * wk[e];
+      }
+      an = warp_sum(an);
+      in = warp_sum(in);
+      // ||G||_F ||G^-1||_F < 1/(2 rtol), compared squared
+      if (tid == 0) sred[1] = (ok && isfinite(in) && an * in < 0.25 / (rtol * rtol)) ? 1.0 : 0.0;
+    }
   }
   __syncthreads();
   if (sred[1] != 0.0) {

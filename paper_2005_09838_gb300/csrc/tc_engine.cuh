@@ -70,8 +70,6 @@ template <typename T>
 using YFn = void (*)(Dev<T>);
 template <typename T>
 using QFn = void (*)(Dev<T>, cx<T>*);
-template <typename T>
-using XbFn = void (*)(Dev<T>, const cx<T>*);
 
 template <typename T>
 inline int pad_rank(int r) {
@@ -282,7 +280,8 @@ class Engine final : public EngineBase {
     const bool s64 = solve64<T>(rp_, mixed_);
     // FP32 engines: room for the FP64 real-slice solve of k_xc (real_gram_solve_store)
     const size_t xa_bytes = (s64 || sizeof(T) == 4) ? xa_smem_bytes<double>(r_) : xa_smem_bytes<T>(r_);
-    xsplit_ = (sizeof(T) == 4 ? rp_ >= 16 : rp_ == 32) && xb_smem_bytes<T>(n1_) <= (size_t)optin &&
+    xsplit_ = (sizeof(T) == 4 ? rp_ >= 16 : rp_ == 32) && xbc_smem_bytes<T>(n1_) <= (size_t)optin &&
+              xbg_smem_bytes<T>(r_) <= (size_t)optin &&
               xa_bytes <= (size_t)optin && xg_smem_bytes<T>(r_) <= (size_t)optin;
     // one-CTA X-step: A^+ of the next X-step formed by k_xa on a graph branch after
     // each Y-step (beside Z~ synthesis and the slab kernel), off the critical path
@@ -313,14 +312,13 @@ class Engine final : public EngineBase {
       xa_threads_ = kXaThreads;
       xa_fn_ = s64 ? k_xa<T, double> : k_xa<T, T>;
       xc_fn_ = s64 ? k_xc<T, double> : k_xc<T, T>;
-      // one CTA per slice when its Q fits in shared memory, else a CTA per 8 columns
-      xb_slice_ = xb1_smem_bytes<T>(n1_, r_) <= (size_t)optin;
-      xb_smem_ = xb_slice_ ? xb1_smem_bytes<T>(n1_, r_) : xb_smem_bytes<T>(n1_);
-      xb_ = xb_slice_ ? k_xb1<T> : k_xb<T>;
+      xbg_smem_ = xbg_smem_bytes<T>(r_);
+      xbc_smem_ = xbc_smem_bytes<T>(n1_);
       xg_smem_ = xg_smem_bytes<T>(r_);
       TC_CUDA_TRY(allow_dynamic_smem((const void*)xa_fn_, xa_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)xc_fn_, xa_smem_));
-      TC_CUDA_TRY(allow_dynamic_smem((const void*)xb_, xb_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xbg<T>, xbg_smem_));
+      TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xbc<T>, xbc_smem_));
       TC_CUDA_TRY(allow_dynamic_smem((const void*)k_xg<T>, xg_smem_));
     }
     ystep_smem_ = ystep_smem_bytes<T>(n1_, r_, rp_);
@@ -846,8 +844,8 @@ class Engine final : public EngineBase {
   // (initialisation, Y-step), so the X-step starts with it in place.
   void launch_xstep(cudaStream_t s) {
     if (xsplit_) {
-      if (xb_slice_) xb_<<<S_, 1024, xb_smem_, s>>>(d_, Q_);
-      else xb_<<<dim3(S_, (r_ + 7) / 8), 256, xb_smem_, s>>>(d_, Q_);
+      k_xbg<T><<<dim3(S_, (n1_ + kXbRows - 1) / kXbRows), 256, xbg_smem_, s>>>(d_, Q_);
+      k_xbc<T><<<dim3(S_, (r_ + 7) / 8), 256, xbc_smem_, s>>>(d_);
       k_xg<T><<<dim3(S_, gch_), 256, xg_smem_, s>>>(d_);
       xc_fn_<<<S_, kXaThreads, xa_smem_, s>>>(d_);
       return;
@@ -949,11 +947,9 @@ class Engine final : public EngineBase {
   int xa_threads_ = kXaThreads;
   YFn<T> xa_fn_ = nullptr, xc_fn_ = nullptr;
   int gch_ = 0;
-  size_t xa_smem_ = 0, xb_smem_ = 0, xg_smem_ = 0;
-  bool xb_slice_ = false;
+  size_t xa_smem_ = 0, xbg_smem_ = 0, xbc_smem_ = 0, xg_smem_ = 0;
   cudaStream_t aux_stream_ = nullptr;  // graph branch of k_xa during capture
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
-  XbFn<T> xb_ = nullptr;
   bool tcy_ = false;  // tensor-core Y-step (D partials, update, Z~ synthesis)
   TcKernels<T> tck_;
   int ksplit_ = 1;

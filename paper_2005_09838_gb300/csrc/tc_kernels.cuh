@@ -62,7 +62,7 @@ struct Dev {
   int yx_global;     // 1: k_ystep reads X~ of the slice from global memory (r n1 too large to stage)
   cx<T>* Dpart;      // [S][ksplit][r][n2] partial D = X~'^H R~ of the tensor-core Y-step
   int ksplit;
-  // X-step of large ranks spread over four kernels (k_xa, k_xb, k_xg, k_xc)
+  // X-step of large ranks spread over five kernels (k_xa, k_xbg, k_xbc, k_xg, k_xc)
   cx<T>* Apg;        // [S][r][r] A^+
   cx<T>* Pg;         // [S][r][r] P = A A^+
   int* certA;        // [S] 1 when A^+ = A^-1 (P = I)
