@@ -290,17 +290,24 @@ __device__ int warp_gj_inverse(const cx<T>* A, cx<T>* Ainv, int r, T& an, T& in)
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
   an = sqrt(a);
   if (!(a > T(0) && isfinite(a))) return 0;
+  // a runtime pivot loop with row p picked by selects: the body (RP rows) is
+  // fetched once and stays in the instruction cache for the later pivots (the
+  // code runs once per launch and CTA, so an unrolled body runs cold)
+#pragma unroll 1
+  for (int p = 0; p < r; ++p) {
+    cx<T> cpv = c[0];
 #pragma unroll
-  for (int p = 0; p < RP; ++p) {
-    if (p >= r) break;
-    const T pv = __shfl_sync(0xffffffffu, c[p].re, p);
+    for (int i = 1; i < RP; ++i)
+      if (i == p) cpv = c[i];
+    const T pv = __shfl_sync(0xffffffffu, cpv.re, p);
     if (!((pv > tiny_pivot<T>()) && isfinite(pv))) return 0;
     const T ip = rcp_refined(pv);
-    const cx<T> rp = c[p] * ip;
+    const cx<T> rp = cpv * ip;
 #pragma unroll
     for (int i = 0; i < RP; ++i) {
       const cx<T> cp = {__shfl_sync(0xffffffffu, c[i].re, p), __shfl_sync(0xffffffffu, c[i].im, p)};
-      c[i] = (i == p) ? rp : c[i] - cmul(cp, rp);
+      const cx<T> u = c[i] - cmul(cp, rp);
+      c[i] = cx<T>{i == p ? rp.re : u.re, i == p ? rp.im : u.im};
     }
   }
   cs = T(0);
@@ -1272,7 +1279,7 @@ __device__ __forceinline__ cx<T> cvt(cx<S> v) {
 // of size 1/lambda_min; their rounding reaches the new Y~ amplified by that
 // condition number.  So on these slices G and Dg are accumulated with
 // error-free products and sums (the callers), the pseudo-inverse is taken in
-// FP64 (df64 arithmetic for r > 16) with the FP64 path's cutoff (d.rtol64), and t G^+ is kept in
+// df64 arithmetic (FP64-class, on the FP32 pipes) with the FP64 path's cutoff (d.rtol64), and t G^+ is kept in
 // FP64 (d.Gp64, slot 0 for k = 0, slot 1 for the Nyquist slice) so that
 // k_ystep applies it in FP64.
 //
@@ -1283,41 +1290,6 @@ __host__ __device__ constexpr size_t real_gram_doubles(int r) { return 7 * (size
 // Where the callers leave G and Dg in M (the layout below).
 __device__ __forceinline__ cx<double>* real_gram_G(cx<double>* M, int) { return M; }
 __device__ __forceinline__ cx<double>* real_gram_Dg(cx<double>* M, int rr) { return M + 6 * rr; }
-
-// Gauss-Jordan inverse (no pivoting) of a real symmetric positive definite
-// r x r matrix in FP64 by the whole block, one element per thread and pivot;
-// a: r^2 doubles (row-major), work: 2 r^2 doubles (the inverse ends in its
-// first half), piv: 2 doubles.  Returns 0 (block-uniform) when a pivot is not
-// positive.  The FP64 pipe is slow on this part, but an 8 x 8 or 16 x 16
-// elimination is a few hundred operations per pivot.
-static __device__ __noinline__ int real_gj_fp64(const double* a, double* work, double* piv, int r) {
-  const int t = threadIdx.x, nt = blockDim.x, rr = r * r;
-  for (int e = t; e < rr; e += nt) work[e] = a[e];
-  // pivot reciprocals: FP32 seed and two Newton steps (an FP64 division is slow here)
-  if (t == 0) piv[0] = (a[0] > 0.0 && isfinite(a[0])) ? rcp_refined(a[0]) : 0.0;
-  __syncthreads();
-  for (int p = 0; p < r; ++p) {
-    const double* src = work + (p & 1) * rr;
-    double* dst = work + ((p + 1) & 1) * rr;
-    const double ip = piv[p & 1];
-    if (!(ip > 0.0)) return 0;
-    for (int e = t; e < rr; e += nt) {
-      const int i = e / r, j = e - i * r;
-      double v;
-      if (i == p) v = (j == p) ? ip : src[p * r + j] * ip;
-      else if (j == p) v = -src[i * r + p] * ip;
-      else v = fma(-src[i * r + p], src[p * r + j] * ip, src[e]);
-      dst[e] = v;
-      if (i == p + 1 && j == p + 1) piv[(p + 1) & 1] = (v > 0.0 && isfinite(v)) ? rcp_refined(v) : 0.0;
-    }
-    __syncthreads();
-  }
-  if (r & 1) {
-    for (int e = t; e < rr; e += nt) work[e] = work[rr + e];
-    __syncthreads();
-  }
-  return 1;
-}
 
 template <typename T, int RP>
 __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<double>* M) {
@@ -1337,7 +1309,7 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
     jacobi_fallback<double, true>(G64, Ap64, P64, V64, W64, piv64, r, rtol, sred + 2);
     __syncthreads();
   }
-  // Gauss-Jordan on the real Gram (FP64; df64 for r > 16), accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
+  // Gauss-Jordan on the real Gram (df64), accepted when ||G||_F ||G^-1||_F < 1/(2 rtol)
   // (then lambda_min > rtol lambda_max: nothing is cut, G^+ = G^-1); otherwise the
   // eigendecomposition fallback applies the cutoff
   // With the rank rule on (step 5), only the leading ra x ra block is active: the
@@ -1345,28 +1317,15 @@ __device__ __noinline__ void real_gram_solve_store(const Dev<T>& d, int k, cx<do
   const int ra = d.rk ? d.rk[k] : r, ra2 = ra * ra;
   double* g = reinterpret_cast<double*>(Ap64);      // ra^2 real values of G (compact)
   double* wk = reinterpret_cast<double*>(W64);      // 2 ra^2
-  double* pv = reinterpret_cast<double*>(piv64);    // 2
   for (int e = tid; e < ra2; e += nt) g[e] = G64[(e / ra) * r + e % ra].re;
   __syncthreads();
-  if (ra > 16) {
-    // df64 elimination in registers; the squared norms come with it (FP32)
+  {
+    // df64 elimination in registers (FP64-pipe operations here wait some 250
+    // cycles each, and the elimination is a chain of them); the norms come with it
     const int ok = gj_regs_df(g, wk, ra);
     if (tid == 0) {  // ||G||_F ||G^-1||_F < 1/(2 rtol)
       const double an = g_solve_xch[200], in = g_solve_xch[201];
       sred[1] = (ok && isfinite(in) && isfinite(an) && an * in < 0.5 / rtol) ? 1.0 : 0.0;
-    }
-  } else {
-    const int ok = real_gj_fp64(g, wk, pv, ra);  // every thread of the block
-    if (tid < 32) {
-      double an = 0.0, in = 0.0;
-      for (int e = tid; e < ra2; e += 32) {
-        an += g[e] * g[e];
-        in += wk[e] * wk[e];
-      }
-      an = warp_sum(an);
-      in = warp_sum(in);
-      // ||G||_F ||G^-1||_F < 1/(2 rtol), compared squared
-      if (tid == 0) sred[1] = (ok && isfinite(in) && an * in < 0.25 / (rtol * rtol)) ? 1.0 : 0.0;
     }
   }
   __syncthreads();
@@ -1410,7 +1369,13 @@ __device__ __noinline__ void real_gram_accumulate(const Dev<T>& d, const cx<T>* 
       const cx<T>* xu = Xn + (size_t)u * n1;
       const cx<T>* ou = Xo + (size_t)u * n1;
       T s0 = T(0), c0 = T(0), s1 = T(0), c1 = T(0), s2 = T(0), c2 = T(0);
-      for (int i = q; i < n1; i += tp) {
+      // this thread's rows q, q + tp, ... from a task-dependent start, so that the
+      // tasks of a warp read different banks (rows of the r columns often sit a
+      // multiple of 128 bytes apart)
+      const int K = (n1 - q + tp - 1) / tp;
+      const int off = K > 0 ? ((base + tid) / tp & 7) % K : 0;
+      for (int kk = 0; kk < K; ++kk) {
+        const int i = q + tp * (kk + off < K ? kk + off : kk + off - K);
         const T a = xs[i].re, b = xu[i].re;
         dot2(s0, c0, a, b);
         dot2(s2, c2, a, b - ou[i].re);
@@ -1619,7 +1584,11 @@ __global__ void __launch_bounds__(xstep_threads(RP), 1) k_xstep(Dev<T> d, const 
           const cx<T>* xs = Ts + (size_t)s * n1;
           const cx<T>* xu = Ts + (size_t)u * n1;
           const cx<T>* ou = Xs + (size_t)u * n1;
-          for (int i = q; i < n1; i += tp) {
+          // rows from a task-dependent start: the tasks of a warp read different banks
+          const int K = (n1 - q + tp - 1) / tp;
+          const int off = K > 0 ? ((tid / tp) & 7) % K : 0;
+          for (int kk = 0; kk < K; ++kk) {
+            const int i = q + tp * (kk + off < K ? kk + off : kk + off - K);
             const cx<T> a = xs[i], b = xu[i];
             cfmaconj(a0[t], a, b);
             cfmaconj(dd[t], a, b - ou[i]);
