@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--form", default="plain", choices=["plain", "precision", "batched"])
     ap.add_argument("--no-forms", action="store_true", help="skip the precision / batched / differentiation "
                     "measurements nested in the default line")
+    ap.add_argument("--precision-forms", default="", help="with --form precision: comma-separated subset of "
+                    "fp32, tf32, bf16, tf32_single_pass, bf16_single_pass (default all)")
     return ap.parse_args()
 
 
@@ -522,7 +524,9 @@ def run_precision(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with ClockSampler(0) as clk:
-        res = precision_form(torch, dev, stream, flush, args.steps, args.warmup, with_nmse=not args.no_nmse)
+        names = [n for n in args.precision_forms.split(",") if n] or None
+        res = precision_form(torch, dev, stream, flush, args.steps, args.warmup, names=names,
+                             with_nmse=not args.no_nmse)
     rates = res["iters_per_s"]
     w = wl.c3(0.3)
     line = {"metric": "completion iters/s, precision form (TF32 tensor-core contractions, FP64-storage solves) "
@@ -534,7 +538,7 @@ def run_precision(args):
                        "l2": "flushed before every timed step", "entries_per_s": rates["tf32"] * w.N},
             "forms_iters_per_s": rates, "speedup_vs_fp32": res["speedup_vs_fp32"],
             "kernel_ms_after_30_iters": res["kernel_ms_after_30_iters"], "nmse": res["nmse"],
-            "nmse_abs_diff_vs_fp64": res["nmse_abs_diff_vs_fp64"], "gpu_launches_per_iter": 6,
+            "nmse_abs_diff_vs_fp64": res["nmse_abs_diff_vs_fp64"], "gpu_launches_per_iter": 10,  # qcon_tc, xbg, xbc, xg, xc, dcon_tc, ystep, zsyn_tc, slab; xa on a branch
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
