@@ -78,3 +78,23 @@ def test_single_pass_error_is_reported(precision, bound):
     w = wl.custom(200, 96, 12, 32, 0.3, seed=7400, iters=10)
     inst, ref, got = _pair(w, precision, w.iters, single_pass=True)
     _check(inst, ref, got, bound, f"single-pass {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_ill_conditioned_gram_takes_the_df64_solve(precision):
+    # Y0 with two rows 3% apart: A = Y~Y~^H of every slice has condition number
+    # near 2e3 at the first X-step.  The FP32 elimination of the refined
+    # inverse then leaves ||I - A X0||_F far above its 2^-14 bar, so the A^+ of
+    # that step comes from the df64 elimination (the fallback branch of the
+    # FP64-storage solve); W and f0 are held to the oracle's at 1e-3.
+    from paper_2005_09838_gb300 import api
+    w = wl.custom(200, 96, 12, 24, 0.5, seed=31)
+    inst = wl.as_precision(wl.generate(w), np.float32)
+    rng = np.random.default_rng(5)
+    Y0 = inst["Y0"].copy()
+    Y0[1] = Y0[0] + 0.03 * rng.standard_normal(Y0[0].shape)
+    Y0 = Y0.astype(np.float32).astype(np.float64)
+    ref = O.tctf2r(inst["G"], inst["mask"], w.r, *SETTING, Y0, iters=3)
+    got = api.complete(inst["G"], inst["mask"], Y0, w.r, 3, *SETTING, precision)
+    assert np.all(np.isfinite(got["W"]))
+    _check(inst, ref, got, TOL, f"{precision} ill-conditioned A, r = 24")
