@@ -272,8 +272,8 @@ class Engine final : public EngineBase {
     }
     xstep_ = pick_xstep_for<T>(rp_, mixed_);
     TC_CUDA_TRY(allow_dynamic_smem((const void*)xstep_, xstep_smem_));
-    // r > 16: the X-step spread over four kernels (k_xsplit.cuh)
-    // the X-step as four kernels (k_xsplit.cuh) for r > 8 in FP32 engines and
+    // the X-step as four kernels spread over the GPU (k_xbg, k_xbc, k_xg, k_xc in
+    // k_xsplit.cuh; A^+ by k_xa on a graph branch) for r > 8 in FP32 engines and
     // r > 16 in the FP64 engine; below that one CTA per slice is faster (the
     // r x r work is small and the extra launches and barriers dominate: 35 us
     // against 49 us for the 144 x 288 x 168, r = 8 workload)
