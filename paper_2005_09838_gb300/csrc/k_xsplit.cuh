@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(256) k_xbg(Dev<T> d, const cx<T>* __restrict__
 // stencil reads every column) X~' goes to d.Tb and k_xc copies it back.
 template <typename T>
 __host__ __device__ inline size_t xbc_smem_bytes(int n1) {
-  return align_up(2 * (size_t)n1 * sizeof(T), 16) + 8 * (size_t)n1 * sizeof(cx<T>);
+  // H_rho1 tables, then per warp its column of B (then d_X) and of X~
+  return align_up(2 * (size_t)n1 * sizeof(T), 16) + 2 * 8 * (size_t)n1 * sizeof(cx<T>);
 }
 
 template <typename T>
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(256) k_xbc(Dev<T> d) {
   T* hinv = reinterpret_cast<T*>(smem);
   T* ha = hinv + n1;
   cx<T>* col = reinterpret_cast<cx<T>*>(smem + align_up(2 * (size_t)n1 * sizeof(T), 16)) + (size_t)wid * n1;
+  cx<T>* xsm = col + 8 * (size_t)n1;  // the warp's column of X~ (read once from L2)
   for (int i = tid; i < 2 * n1; i += blockDim.x) hinv[i] = d.hinv[i];
   __syncthreads();
   const bool realslice = (k == 0) || (2 * k == d.n3);
@@ -242,17 +244,24 @@ __global__ void __launch_bounds__(256) k_xbc(Dev<T> d) {
     cx<T>* bs = d.Tb + (size_t)k * r * n1 + (size_t)s * n1;
     {
       int i = lane;
-      for (; i + 96 < n1; i += 128) {  // four pairs of loads in flight per lane
-        cx<T> b[4], x[4];
+      for (; i + 224 < n1; i += 256) {  // eight pairs of loads in flight per lane
+        cx<T> b[8], x[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
           b[q] = bs[i + 32 * q];
           x[q] = xs[i + 32 * q];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) col[i + 32 * q] = fast ? b[q] + x[q] : b[q];
+        for (int q = 0; q < 8; ++q) {
+          col[i + 32 * q] = fast ? b[q] + x[q] : b[q];
+          xsm[i + 32 * q] = x[q];
+        }
       }
-      for (; i < n1; i += 32) col[i] = fast ? bs[i] + xs[i] : bs[i];
+      for (; i < n1; i += 32) {
+        const cx<T> b = bs[i], x = xs[i];
+        col[i] = fast ? b + x : b;
+        xsm[i] = x;
+      }
     }
     if (!fast && rho1 != T(0)) {
       const cx<T>* pg = d.Pg + (size_t)k * rr;
@@ -280,15 +289,7 @@ __global__ void __launch_bounds__(256) k_xbc(Dev<T> d) {
       }
       if (d.conv) dmax = fmax(dmax, (double)cabs(v - x0));
     };
-    int i = lane;
-    for (; i + 96 < n1; i += 128) {  // four loads in flight per lane
-      cx<T> x0[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) x0[q] = xs[i + 32 * q];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) update(i + 32 * q, x0[q]);
-    }
-    for (; i < n1; i += 32) update(i, xs[i]);
+    for (int i = lane; i < n1; i += 32) update(i, xsm[i]);
   }
   if (d.conv) block_max_to(dmax, d.conv + 0);
 }
