@@ -200,13 +200,23 @@ def test_c2_full_size_three_iterations_fp32():
 
 @pytest.mark.parametrize("precision,n1", [("fp32", 1000), ("fp64", 700)])
 def test_rank32_longest_slices(precision, n1):
-    # r = 32 with the slice's Q too large for one CTA's shared memory: the
-    # X-step forms B with one CTA per 8 columns (FP32: Q staged per CTA; FP64:
-    # read through L1)
+    # r = 32 with long slices (n1 = 1000 / 700): B = QA^+ over eight 128-row
+    # chunks per slice, the column update and Gram partials over many chunks
     w = wl.custom(n1, 40, 8, 32, 0.3, seed=3200 + n1, iters=6)
     inst, ref, got = _run_pair(w, "R", precision, w.iters)
     assert _rel(got["W"], ref["W"]) <= TOL[precision]
     assert abs(got["f0"] - ref["f0"]) <= TOL[precision] * abs(ref["f0"])
+
+
+@pytest.mark.parametrize("r", [12, 16])
+def test_fp32_middle_ranks(r):
+    # 8 < r <= 16 in an FP32 engine: the X-step spread over the GPU with the
+    # r <= 16 layout of the B = QA^+ tiles (four column groups per warp) and the
+    # r x r solves in FP32 storage; n1 = 150 (two ragged 128-row chunks)
+    w = wl.custom(150, 48, 12, r, 0.4, seed=4100 + r, iters=8)
+    inst, ref, got = _run_pair(w, "R", "fp32", w.iters)
+    assert _rel(got["W"], ref["W"]) <= TOL["fp32"]
+    assert abs(got["f0"] - ref["f0"]) <= TOL["fp32"] * abs(ref["f0"])
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
